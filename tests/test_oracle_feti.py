@@ -1,0 +1,105 @@
+"""Pins of the oracle's FETI solve: agreement with the monolithic solution (Theorem 3.1),
+operator properties, coarse constraints, Krylov methods against dense solves."""
+import numpy as np
+import pytest
+
+from oracle.monolithic import Discretization, solve_monolithic
+from oracle.feti import FETI, pcg, minres
+from paper_2509_06673_gb300 import workloads as W
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("krylov", ["pcg", "minres"])
+@pytest.mark.parametrize("case", [
+    W.config1(n_steps=3),
+    W.small_case(4, 4, 3, k=2, lame_lambda=49.0, tau=1e-3, n_steps=2, tol=1e-12),
+    W.grid_case("uneven", 3, 4, [2, 4, 3], [3, 2, 4, 3], order_k=1, lame_lambda=5.0,
+                c0=0.5, tau=1e-2, n_steps=2, tol=1e-12),
+])
+def test_feti_equals_monolithic(case, krylov):
+    d = Discretization(case)
+    mono = solve_monolithic(case, d)
+    fe = FETI(case, d).run(krylov=krylov)
+    for a, b in zip(mono, fe):
+        assert _rel(b["lambda"], a["lambda"]) < 1e-8
+        for fa, fb in zip(a["fields"], b["fields"]):
+            for xa, xb in zip(fa, fb):
+                if xa is not None:
+                    assert np.abs(xa - xb).max() < 1e-8 * max(1.0, np.abs(xa).max())
+
+
+def _small():
+    c = W.small_case(4, 4, 2, k=2, lame_lambda=49.0, tau=1e-3, n_steps=1, tol=1e-12)
+    d = Discretization(c)
+    return c, d, FETI(c, d)
+
+
+def test_operator_properties():
+    c, d, f = _small()
+    I = d.iface
+    n = I.n_lambda
+    B = np.hstack([Bs.toarray() for Bs in I.Bs])
+    assert np.linalg.matrix_rank(B) == n                      # non-redundant multipliers
+    for s in I.floating:                                       # K_s R_s = 0
+        assert np.abs(d.locals[s].K @ I.Rs[s]).max() < 1e-10
+    Fd = f.dense_F()
+    assert np.abs(Fd - Fd.T).max() < 1e-10 * np.abs(Fd).max()
+    # inertia on range(P): positive for displacement rows, negative for pressure rows
+    E = np.eye(n)
+    P = np.column_stack([f.P(E[:, j]) for j in range(n)])
+    U, sv, _ = np.linalg.svd(P)
+    Q = U[:, sv > 0.5]
+    ev = np.linalg.eigvalsh(Q.T @ Fd @ Q)
+    assert (ev < 0).sum() == I.is_p.sum()
+    assert (ev > 0).sum() == Q.shape[1] - I.is_p.sum()
+    # preconditioned operator: real spectrum >= ~1 on range(P) (the reason Algorithm 1 is used)
+    M = np.column_stack([f.precond(E[:, j]) for j in range(n)])
+    mu = np.linalg.eigvals(np.linalg.solve(np.eye(Q.shape[1]), (Q.T @ M @ Q) @ (Q.T @ Fd @ Q)))
+    assert mu.real.min() > 0.9 and np.abs(mu.imag).max() < 1e-2 * mu.real.max()
+
+
+def test_coarse_constraint_and_continuity():
+    c, d, f = _small()
+    I = d.iface
+    Reta = d.initial_Reta()
+    fl = [L.rhs(c.tau, Reta[s]) for s, L in enumerate(d.locals)]
+    lam, its, hist, dd = f.solve_step(fl, np.zeros(I.n_lambda))
+    assert np.abs(I.G.T @ lam - I.e_vector(fl)).max() < 1e-9 * np.abs(I.e_vector(fl)).max()
+    xs = f.recover(fl, lam, dd)
+    jump = sum(B @ x for B, x in zip(I.Bs, xs))
+    assert np.abs(jump).max() < 1e-9 * max(np.abs(x).max() for x in xs)
+    for s, L in enumerate(d.locals):  # every local equation K_s x_s + B_s^T lambda = f_s
+        res = L.K @ xs[s] + I.Bs[s].T @ lam - fl[s]
+        assert np.abs(res).max() < 1e-8 * np.abs(fl[s]).max()
+
+
+def test_fixed_dofs_do_not_change_solution():
+    c, d, f = _small()
+    Reta = d.initial_Reta()
+    fl = [L.rhs(c.tau, Reta[s]) for s, L in enumerate(d.locals)]
+    lam, _, _, dd = f.solve_step(fl, np.zeros(d.iface.n_lambda))
+    xs = f.recover(fl, lam, dd)
+    f2 = FETI(c, d, fixed_override=lambda s, L: np.array([2 * 4, 2 * 4 + 1, 2 * (L.m.n_unode - 1)]))
+    lam2, _, _, dd2 = f2.solve_step(fl, np.zeros(d.iface.n_lambda))
+    xs2 = f2.recover(fl, lam2, dd2)
+    assert _rel(lam2, lam) < 1e-8
+    for a, b in zip(xs, xs2):
+        assert np.abs(a - b).max() < 1e-8 * np.abs(a).max()
+
+
+def test_krylov_against_dense():
+    rng = np.random.default_rng(3)
+    n = 60
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    A_spd = Q @ np.diag(rng.uniform(1, 50, n)) @ Q.T
+    A_ind = Q @ np.diag(np.r_[rng.uniform(1, 50, 40), -rng.uniform(1, 20, 20)]) @ Q.T
+    Mi = np.diag(rng.uniform(0.5, 2, n))
+    b = rng.normal(size=n)
+    x, k, h = pcg(lambda v: A_spd @ v, lambda v: Mi @ v, b, np.zeros(n), 1e-12, np.linalg.norm(b), 500)
+    assert _rel(x, np.linalg.solve(A_spd, b)) < 1e-9
+    x, k, h = minres(lambda v: A_ind @ v, lambda v: Mi @ v, b, np.zeros(n), 1e-12, np.linalg.norm(b), 500)
+    assert _rel(x, np.linalg.solve(A_ind, b)) < 1e-9
+    assert abs(h[-1] - np.linalg.norm(b - A_ind @ x)) < 1e-10 * np.linalg.norm(b)
