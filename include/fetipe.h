@@ -1,0 +1,193 @@
+/*
+ * fetipe -- FETI interface solver for quasi-static poroelasticity coupled with elasticity,
+ * multiphysics finite elements, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Ge & Wang, "A Parallel Solver with Multiphysics Finite Element Method for
+ * Poroelasticity Coupled with Elasticity Model", arXiv 2509.06673.
+ *
+ * Problem statement (Sec. 2.5, Problem 2.4): given a triangulation of the unit square
+ * Omega = Omega^P (y < 1/2, Biot poroelasticity) U Omega^E (y > 1/2, linear elasticity),
+ * parameters (Table 2), boundary and initial data, compute for n = 1..N the backward-Euler
+ * solution (u_h^n, xi_h^n, eta_h^n, p_h^n) and the interface multiplier lambda_h^n.
+ * Each step is solved by FETI (Sec. 3): PCG (Algorithm 1) on F lambda = d with
+ * F = sum_s B_s K_s^+ B_s^T (Eq. (3.6)) and the Dirichlet preconditioner (Eq. (3.5)),
+ * plus the FETI-1 rigid-mode coarse projection for floating subdomains.
+ *
+ * Conventions of every call:
+ *  - All calls return fp_status; FP_OK is 0.  fp_last_error() gives a message.
+ *  - No call aborts the process.  A failed call leaves the handle valid; calls that need
+ *    an earlier stage (fp_step before fp_factor, ...) return FP_ERR_STATE.
+ *  - Input arrays are copied during the call; the caller keeps ownership.
+ *  - Output arrays are caller-owned.  `on_device` = 0: host memory; 1: device memory of
+ *    the handle's device (e.g. a torch tensor's data_ptr()).
+ *  - One CUDA stream per handle (the `cuda_stream` given to fp_create; NULL = legacy
+ *    default stream).  Calls are synchronous with respect to the host unless stated.
+ *  - The handle owns all the device memory it allocates; fp_destroy frees it.
+ */
+#ifndef FETIPE_H
+#define FETIPE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fp_handle fp_handle;
+
+typedef enum {
+  FP_OK = 0,
+  FP_ERR_INVALID = 1,        /* bad argument or inconsistent mesh/partition */
+  FP_ERR_OOM = 2,            /* device or host allocation failed */
+  FP_ERR_CUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error) */
+  FP_ERR_NOT_CONVERGED = 4,  /* max_it reached before the stop test held */
+  FP_ERR_BREAKDOWN = 5,      /* PCG breakdown (p^T F p = 0 or non-finite values) */
+  FP_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  FP_ERR_STATE = 7           /* call out of order (e.g. fp_step before fp_factor) */
+} fp_status;
+
+enum { FP_SOURCE_MANUFACTURED = 0, FP_SOURCE_POINT = 1 };
+enum { FP_PREC_FP64 = 0, FP_PREC_MIXED = 1 };
+enum { FP_PRECOND_DIRICHLET = 0, FP_PRECOND_NONE = 2 };
+
+/*
+ * Partition and mesh (Sec. 2.4; Sec. 4.1 uses uniform triangulations).  The unit square is
+ * cut into nsub_x x nsub_y rectangular subdomains, numbered s = cy * nsub_x + cx from the
+ * bottom-left.  Partition column cx has cells_x[cx] cells across, partition row cy has
+ * cells_y[cy] cells up, so meshes match on every interface.  Rows cy < poro_rows are
+ * poroelastic (poro_rows = nsub_y / 2 puts the P/E interface at y = 1/2).  Every cell is
+ * cut by its '/' diagonal into triangles (v00, v10, v11) and (v00, v11, v01); element
+ * e = 2 * (j * nx + i) + t within a subdomain.  Displacement: P_k, k = order_k (1 or 2);
+ * xi, eta, p: P1 (Sec. 2.4).  u = 0 on the boundary of the square; p = 0 on the outer
+ * boundary of Omega^P (no-flux on y = 1/2, Eq. (2.14)).
+ */
+typedef struct {
+  int nsub_x, nsub_y;
+  const int *cells_x;   /* [nsub_x], each >= 1 */
+  const int *cells_y;   /* [nsub_y], each >= 1 */
+  int poro_rows;        /* 1 <= poro_rows < nsub_y */
+  int order_k;          /* 1 or 2 */
+} fp_mesh_desc;
+
+/*
+ * Physical and solver parameters (Table 2 of the paper; the multiphysics constants
+ * kappa_1..3 of Sec. 2.2 follow from lame_lambda, alpha, c0).
+ *  perm: NULL (uniform perm_k) or one value per element of every subdomain, subdomains in
+ *        id order, elements in the order above (host pointer, copied).
+ *  source: FP_SOURCE_MANUFACTURED -- the closed-form solution of Test Case 1 (Sec. 4.1)
+ *            with its sources; eta^0 is the L2 projection of c0 p + alpha div u.
+ *          FP_SOURCE_POINT -- f = 0 and a point fluid source z = sin(q_omega t) at the P1
+ *            vertex with global P1 grid indices (src_i, src_j) (must lie strictly inside
+ *            one poroelastic subdomain); zero initial data.
+ *  precision: FP_PREC_FP64 -- local factors and solves in FP64.
+ *             FP_PREC_MIXED -- local factors and solves in FP32, outer PCG, coarse problem
+ *             and refinement residuals in FP64.
+ *  tol: PCG stops when ||P(d - F lambda)||_2 <= tol * ||P(d - F lambda_00)||_2.
+ */
+typedef struct {
+  double lame_lambda, mu, alpha, c0;
+  double perm_k, mu_f;
+  double tau;
+  const double *perm;
+  int source;
+  int src_i, src_j;
+  double q_omega;
+  int precision;
+  int precond;
+  double tol;
+  int max_it;
+} fp_params;
+
+typedef struct {
+  int nsub, n_floating, n_lambda, n_lambda_p;
+  long long n_dofs;          /* sum of local 3-field dofs (u, xi, p) */
+  long long n_unode_total;   /* length of the u field / 2 in fp_get_fields */
+  long long n_pnode_total;   /* length of xi, eta, p in fp_get_fields */
+  long long factor_bytes;    /* device bytes of all local factors */
+  int max_half_band;
+} fp_sizes;
+
+typedef struct {
+  int step;                  /* n of the step just solved */
+  int iterations;            /* PCG iterations */
+  double rel_residual;       /* recursive ||P r|| / ||P(d - F lambda_00)|| at exit */
+  double true_rel_residual;  /* the same with r recomputed from lambda at exit */
+} fp_step_stats;
+
+/* Copies the mesh description and parameters, builds the dof numbering, band ordering and
+ * interface tables on the host and uploads them to the current device.
+ * cuda_stream: a cudaStream_t (NULL = default stream).  Errors: FP_ERR_INVALID, FP_ERR_OOM,
+ * FP_ERR_CUDA.  *out is NULL on error. */
+fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cuda_stream,
+                    fp_handle **out);
+
+/* Assembles every local matrix (the 3-field blocks of Sec. 3.1 with eta eliminated, see
+ * below) and load vector on the device, and the coarse matrix G^T G.  Time-invariant
+ * (tau is fixed, Sec. 2.5), so called once.  Local 3-field block of a poroelastic
+ * subdomain, unknowns (u, xi, p):
+ *   [ A        B^T            0                          ]
+ *   [ B      -R/lambda       (alpha/lambda) R            ]
+ *   [ 0      (alpha/lambda) R  -((c0 + alpha^2/lambda) R + tau A_f) ]
+ * obtained from Eq. (2.43) by eta = (p - kappa_1 xi) / kappa_2 (exact since W_h = M_h^P);
+ * elastic: [[A, B^T], [B, -R/lambda]]. */
+fp_status fp_assemble(fp_handle *h);
+
+/* Factors every local matrix: LDL^T (no pivoting; the 3-field blocks are symmetric
+ * quasi-definite) of the Neumann matrix K_s (three displacement dofs fixed on floating
+ * subdomains, giving the generalised inverse K_s^+) and of the Dirichlet matrix (K_s with
+ * identity rows on the dofs touched by B_s, giving S_s of Eq. (3.5)), and the coarse
+ * inverse (G^T G)^{-1}.  Idempotent. */
+fp_status fp_factor(fp_handle *h);
+
+/* Solves one backward-Euler step (Problem 2.4) with FETI: right-hand side, d = B K^+ f,
+ * lambda_0 from lambda^{n-1} (Algorithm 1) projected onto G^T lambda = e, PCG, recovery of
+ * (u, xi, p) per subdomain and eta = (c0 + alpha^2/lambda) p - (alpha/lambda) xi.
+ * stats may be NULL.  Returns FP_ERR_NOT_CONVERGED / FP_ERR_BREAKDOWN with the state of
+ * the last iterate kept. */
+fp_status fp_step(fp_handle *h, fp_step_stats *stats);
+
+/* Runs n_steps steps back to back (same as calling fp_step n_steps times). */
+fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last);
+
+fp_status fp_get_sizes(const fp_handle *h, fp_sizes *out);
+
+/* lambda^n of the last step, n_lambda doubles.  Multiplier r enforces
+ * x_{s_a} - x_{s_b} = 0 on one node component (see fp_get_lambda_keys). */
+fp_status fp_get_lambda(const fp_handle *h, double *dst, int on_device);
+
+/* Six ints per multiplier (host): kind (0 displacement, 1 pressure), component (0/1),
+ * global grid index I, J (displacement grid of order k for kind 0, P1 grid for kind 1),
+ * s_a, s_b (s_a < s_b; the row is +1 on s_a, -1 on s_b). */
+fp_status fp_get_lambda_keys(const fp_handle *h, int *keys);
+
+/* Fields of the last step on the subdomain node grids, subdomains in id order:
+ * u: 2 doubles per displacement node ((k*ny+1) x (k*nx+1) per subdomain, row-major, x
+ * fastest); xi, eta, p: one double per P1 node ((ny+1) x (nx+1) per subdomain); eta and p
+ * are zero on elastic subdomains.  Any pointer may be NULL. */
+fp_status fp_get_fields(const fp_handle *h, double *u, double *xi, double *eta, double *p,
+                        int on_device);
+
+/* Operator applications on multiplier vectors of length n_lambda (after fp_factor):
+ * out = F v (Eq. (3.6)), out = M^{-1} v (Eq. (3.5), scaled by W = (B B^T)^{-1} on both
+ * sides), out = P v (coarse projection).  v and out may not alias. */
+fp_status fp_apply_F(fp_handle *h, const double *v, double *out, int on_device);
+fp_status fp_apply_precond(fp_handle *h, const double *v, double *out, int on_device);
+fp_status fp_apply_projection(fp_handle *h, const double *v, double *out, int on_device);
+
+/* Local dof map of subdomain s (host, n_s ints each): field (0 u_x, 1 u_y, 2 xi, 3 p) and
+ * node index on the subdomain's grid (displacement grid for u, P1 grid otherwise). */
+fp_status fp_get_dof_map(const fp_handle *h, int s, int *field, int *node, int *n_out);
+
+/* Dense copy (host, n_s * n_s doubles, row-major) of the assembled local matrix of
+ * subdomain s in its band ordering (lower band mirrored).  For tests of small subdomains. */
+fp_status fp_get_local_matrix(const fp_handle *h, int s, double *dense);
+
+/* Device time of the last fp_step split by phase (milliseconds, CUDA events):
+ * [0] rhs + d, [1] PCG loop, [2] recovery; [3] total local-solve time of the step. */
+fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
+
+const char *fp_last_error(const fp_handle *h);
+void fp_destroy(fp_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FETIPE_H */

@@ -1,0 +1,700 @@
+// C ABI of the fetipe library: handle lifecycle and the orchestration of one
+// backward-Euler step (Sec. 2.5) solved by FETI (Sec. 3, Algorithm 1).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace fp {
+// kernels (defined in the other translation units)
+__global__ void k_assemble(DevTopo, DevParams, double *, double *, double *, double *);
+cudaError_t launch_csr_to_band(bool fp32, DevTopo D, const double *csr_val, void *band, int mode, cudaStream_t s);
+__global__ void k_coarse_G(DevTopo, double *, double *);
+__global__ void k_coarse_GtG(DevTopo, const double *, const double *, double *);
+cudaError_t launch_band_factor(bool fp32, const BandTask *tasks, int ntask, void *base, int NB, int *status,
+                               size_t smem, cudaStream_t stream);
+cudaError_t launch_band_solve(bool fp32, int mmax, int grid, int wpc, cudaStream_t stream, const BandTask *tasks,
+                              int ntask, const void *fac, double *x, int *counter, int *status, const int *done);
+__global__ void k_dot(const double *, const double *, long long, double *, unsigned *, double *, int *, int,
+                      double *, int);
+__global__ void k_pcg_update(double *, double *, const double *, const double *, long long, double *, unsigned *,
+                             double *, int *);
+__global__ void k_pcg_pupdate(double *, const double *, long long, const double *, const int *);
+__global__ void k_lincomb(double *, const double *, double, const double *, double, long long, const int *);
+__global__ void k_scatter(DevTopo, const double *, double, double *, int, const int *);
+__global__ void k_gather(DevTopo, const double *, double *, const int *);
+__global__ void k_wscale(DevTopo, const double *, double *, const int *);
+__global__ void k_halo(DevTopo, const double *, const double *, double *, const int *);
+__global__ void k_bnd_apply(DevTopo, const double *, const double *, double *, const int *);
+__global__ void k_Gt(DevTopo, const double *, double *, const int *);
+__global__ void k_gemv(const double *, const double *, double *, int, const int *);
+__global__ void k_Gcomb(DevTopo, const double *, const double *, double, double *, const int *);
+__global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, double, double *,
+                      double *);
+__global__ void k_recover(DevTopo, DevParams, const double *, const double *, const double *, double *, double *,
+                          double *, double *, double *);
+cudaError_t launch_band_to_dense(const double *band, int n, int LD, int b, double *out, cudaStream_t s);
+__global__ void k_identity(double *, int);
+
+}  // namespace fp
+
+using namespace fp;
+
+struct fp_handle {
+  Topology T;
+  fp_params P{};
+  std::vector<double> perm;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 148;
+  std::string err;
+  int stage = 0;  // 0 created, 1 assembled, 2 factored
+  int step_n = 0;
+  std::vector<void *> allocs;
+  // device topology
+  DevTopo D{};
+  DevParams DP{};
+  // matrices
+  double *csr_val = nullptr, *fstat = nullptr, *Zn = nullptr, *E0n = nullptr, *Reta = nullptr;
+  void *facN = nullptr, *facD = nullptr;
+  double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
+  BandTask *tasksN = nullptr, *tasksD = nullptr, *taskH = nullptr, *tasksHinv = nullptr;
+  int ntask = 0, mmax = 4, mmaxH = 4, ldmax = 32;
+  int *counter = nullptr, *status = nullptr;
+  // vectors
+  double *X2 = nullptr, *XB = nullptr, *XP = nullptr, *XY = nullptr;
+  double *lam = nullptr, *lam_prev = nullptr, *lam00 = nullptr, *d = nullptr, *r = nullptr, *z = nullptr,
+         *p = nullptr, *q = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double *ce = nullptr, *cy = nullptr, *calpha = nullptr;
+  double *partial = nullptr, *sc = nullptr;
+  unsigned *red_counter = nullptr;
+  int *fl = nullptr, *fl_zero = nullptr, *h_fl = nullptr;
+  double *h_sc = nullptr;
+  double *U = nullptr, *XI = nullptr, *ETA = nullptr, *PP = nullptr;
+  cudaEvent_t ev[6] = {};
+  double last_ms[4] = {0, 0, 0, 0};
+  int nbnd_max = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+      return e_ == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA;           \
+    }                                                                             \
+  } while (0)
+
+#define CKL()                                                                     \
+  do {                                                                            \
+    cudaError_t e_ = cudaGetLastError();                                          \
+    if (e_ != cudaSuccess) {                                                      \
+      h->err = std::string("kernel launch: ") + cudaGetErrorString(e_);           \
+      return FP_ERR_CUDA;                                                         \
+    }                                                                             \
+  } while (0)
+
+template <typename V>
+fp_status dalloc(fp_handle *h, V **ptr, size_t count) {
+  void *p = nullptr;
+  CK(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(V)));
+  h->allocs.push_back(p);
+  *ptr = static_cast<V *>(p);
+  return FP_OK;
+}
+
+template <typename V>
+fp_status upload(fp_handle *h, const V **dst, const std::vector<V> &src) {
+  V *p = nullptr;
+  fp_status st = dalloc(h, &p, src.size());
+  if (st) return st;
+  if (!src.empty()) CK(cudaMemcpyAsync(p, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice, h->stream));
+  *dst = p;
+  return FP_OK;
+}
+
+#define TRY(x)                 \
+  do {                         \
+    fp_status s_ = (x);        \
+    if (s_ != FP_OK) return s_; \
+  } while (0)
+
+unsigned grid_for(long long n, int block) { return (unsigned)std::min<long long>((n + block - 1) / block, 65535LL * 16); }
+
+fp_status build_device(fp_handle *h) {
+  Topology &T = h->T;
+  // ---- template pool ----
+  std::vector<int> pool;
+  std::vector<DevTpl> tpls;
+  auto put = [&](const std::vector<int> &v) {
+    long long off = (long long)pool.size();
+    pool.insert(pool.end(), v.begin(), v.end());
+    return off;
+  };
+  for (const Template &t : T.tpl) {
+    DevTpl d{};
+    d.n = t.n; d.b = t.b; d.LD = t.LD; d.k = t.k; d.poro = t.poro; d.nx = t.nx; d.ny = t.ny;
+    d.nux = t.nux; d.nuy = t.nuy; d.npx = t.npx; d.npy = t.npy; d.ndl = t.ndl; d.floating = t.floating;
+    d.fixed0 = t.fixed[0]; d.fixed1 = t.fixed[1]; d.fixed2 = t.fixed[2];
+    d.nbnd = (int)t.bnd.size(); d.nhalo = (int)t.halo_row.size(); d.nnz = (int)t.csr_col.size();
+    d.udof = put(t.udof); d.xidof = put(t.xidof); d.pdof = put(t.pdof);
+    d.dof_field = put(t.dof_field); d.dof_node = put(t.dof_node);
+    d.csr_ptr = put(t.csr_ptr); d.csr_col = put(t.csr_col);
+    d.bnd = put(t.bnd);
+    std::vector<int> isb(t.is_bnd.begin(), t.is_bnd.end());
+    d.is_bnd = put(isb);
+    d.halo_ptr = put(t.halo_ptr); d.halo_row = put(t.halo_row); d.halo_ent = put(t.halo_ent);
+    d.elem_dofs = put(t.elem_dofs);
+    tpls.push_back(d);
+    h->nbnd_max = std::max(h->nbnd_max, d.nbnd);
+    h->ldmax = std::max(h->ldmax, t.LD);
+  }
+  DevTopo &D = h->D;
+  D.S = T.S; D.NF = T.NF; D.nlam = T.n_lambda; D.nH = T.nH; D.bH = T.bH; D.LDH = T.LDH; D.k = T.k;
+  D.nsx = T.nsx; D.nsy = T.nsy;
+  TRY(upload(h, &D.tpl, tpls));
+  TRY(upload(h, &D.pool, pool));
+  TRY(upload(h, &D.sub_tpl, T.sub_tpl));
+  TRY(upload(h, &D.sub_x0, T.sub_x0)); TRY(upload(h, &D.sub_y0, T.sub_y0));
+  TRY(upload(h, &D.sub_hx, T.sub_hx)); TRY(upload(h, &D.sub_hy, T.sub_hy));
+  TRY(upload(h, &D.vec_off, T.vec_off)); TRY(upload(h, &D.fac_off, T.fac_off));
+  TRY(upload(h, &D.csr_off, T.csr_off)); TRY(upload(h, &D.unode_off, T.unode_off));
+  TRY(upload(h, &D.pnode_off, T.pnode_off)); TRY(upload(h, &D.elem_off, T.elem_off));
+  TRY(upload(h, &D.bsc_off, T.bsc_off));
+  TRY(upload(h, &D.sub_I0, T.sub_I0)); TRY(upload(h, &D.sub_J0, T.sub_J0));
+  TRY(upload(h, &D.lam_sa, T.lam_sa)); TRY(upload(h, &D.lam_da, T.lam_da));
+  TRY(upload(h, &D.lam_sb, T.lam_sb)); TRY(upload(h, &D.lam_db, T.lam_db));
+  std::vector<int> kind(T.n_lambda);
+  for (int r = 0; r < T.n_lambda; ++r) kind[r] = T.lam_key[6 * r];
+  TRY(upload(h, &D.lam_kind, kind));
+  TRY(upload(h, &D.wgrp_first, T.wgrp_first)); TRY(upload(h, &D.wgrp_size, T.wgrp_size));
+  D.nwgrp = (int)T.wgrp_first.size();
+  TRY(upload(h, &D.bsc_row, T.bsc_row)); TRY(upload(h, &D.bsc_sign, T.bsc_sign));
+  TRY(upload(h, &D.sub_float, T.sub_float)); TRY(upload(h, &D.float_sub, T.float_sub));
+  TRY(upload(h, &D.float_rows_ptr, T.float_rows_ptr)); TRY(upload(h, &D.float_rows, T.float_rows));
+  std::vector<int> fa(T.n_lambda), fb(T.n_lambda);
+  for (int r = 0; r < T.n_lambda; ++r) { fa[r] = T.sub_float[T.lam_sa[r]]; fb[r] = T.sub_float[T.lam_sb[r]]; }
+  TRY(upload(h, &D.lam_fa, fa)); TRY(upload(h, &D.lam_fb, fb));
+  TRY(dalloc(h, &h->ga, 3 * (size_t)T.n_lambda));
+  TRY(dalloc(h, &h->gb, 3 * (size_t)T.n_lambda));
+  D.lam_ga = h->ga; D.lam_gb = h->gb;
+  // params
+  DevParams &P = h->DP;
+  P.lam = h->P.lame_lambda; P.mu = h->P.mu; P.alpha = h->P.alpha; P.c0 = h->P.c0;
+  P.perm_k = h->P.perm_k; P.mu_f = h->P.mu_f; P.tau = h->P.tau; P.q_omega = h->P.q_omega;
+  P.source = h->P.source; P.src_sub = T.src_sub; P.src_node = T.src_node;
+  P.perm = nullptr;
+  if (!h->perm.empty()) {
+    const double *pp = nullptr;
+    TRY(upload(h, &pp, h->perm));
+    P.perm = pp;
+  }
+  // ---- tasks (cost-sorted, largest first) ----
+  std::vector<int> order(T.S);
+  for (int s = 0; s < T.S; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const Template &ta = T.tpl[T.sub_tpl[a]], &tb = T.tpl[T.sub_tpl[b]];
+    return (long long)ta.n * ta.LD > (long long)tb.n * tb.LD;
+  });
+  std::vector<BandTask> tk;
+  int mmax = 1;
+  for (int s : order) {
+    const Template &t = T.tpl[T.sub_tpl[s]];
+    tk.push_back({T.fac_off[s], T.vec_off[s], t.n, t.LD, t.b, 0});
+    mmax = std::max(mmax, t.LD / 32);
+  }
+  if (mmax > 16) { h->err = "half bandwidth above 511 is not supported"; return FP_ERR_INVALID; }
+  h->mmax = mmax <= 4 ? 4 : mmax <= 8 ? 8 : mmax <= 12 ? 12 : 16;
+  h->ntask = T.S;
+  const BandTask *dt = nullptr;
+  TRY(upload(h, &dt, tk));
+  h->tasksN = const_cast<BandTask *>(dt);
+  h->tasksD = h->tasksN;  // same offsets; the two factors live in separate arrays
+  if (T.NF) {
+    std::vector<BandTask> th = {{0, 0, T.nH, T.LDH, T.bH, 0}};
+    TRY(upload(h, &dt, th));
+    h->taskH = const_cast<BandTask *>(dt);
+    std::vector<BandTask> ti(T.nH);
+    for (int i = 0; i < T.nH; ++i) ti[i] = {0, (long long)i * T.nH, T.nH, T.LDH, T.bH, 0};
+    TRY(upload(h, &dt, ti));
+    h->tasksHinv = const_cast<BandTask *>(dt);
+    const int mh = T.LDH / 32;
+    if (mh > 16) { h->err = "coarse band too wide"; return FP_ERR_INVALID; }
+    h->mmaxH = mh <= 4 ? 4 : mh <= 8 ? 8 : mh <= 12 ? 12 : 16;
+  }
+  // ---- work arrays ----
+  const long long nv = T.vec_off[T.S], nl = std::max(T.n_lambda, 1);
+  TRY(dalloc(h, &h->csr_val, (size_t)T.csr_off[T.S]));
+  TRY(dalloc(h, &h->fstat, (size_t)nv));
+  TRY(dalloc(h, &h->Zn, (size_t)T.pnode_off[T.S]));
+  TRY(dalloc(h, &h->E0n, (size_t)T.pnode_off[T.S]));
+  TRY(dalloc(h, &h->Reta, (size_t)T.pnode_off[T.S]));
+  for (double **v : {&h->X2, &h->XB, &h->XP, &h->XY}) TRY(dalloc(h, v, (size_t)nv));
+  for (double **v : {&h->lam, &h->lam_prev, &h->lam00, &h->d, &h->r, &h->z, &h->p, &h->q, &h->t1, &h->t2})
+    TRY(dalloc(h, v, (size_t)nl));
+  const size_t nc = std::max(T.nH, 1);
+  for (double **v : {&h->ce, &h->cy, &h->calpha}) TRY(dalloc(h, v, nc));
+  TRY(dalloc(h, &h->partial, RED_BLOCKS));
+  TRY(dalloc(h, &h->sc, SC_N));
+  TRY(dalloc(h, &h->red_counter, 4));
+  TRY(dalloc(h, &h->fl, FL_N));
+  TRY(dalloc(h, &h->fl_zero, FL_N));
+  TRY(dalloc(h, &h->counter, 4));
+  TRY(dalloc(h, &h->status, 4));
+  TRY(dalloc(h, &h->U, 2 * (size_t)T.unode_off[T.S]));
+  TRY(dalloc(h, &h->XI, (size_t)T.pnode_off[T.S]));
+  TRY(dalloc(h, &h->ETA, (size_t)T.pnode_off[T.S]));
+  TRY(dalloc(h, &h->PP, (size_t)T.pnode_off[T.S]));
+  CK(cudaMemsetAsync(h->red_counter, 0, 4 * sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(h->fl_zero, 0, FL_N * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(h->lam_prev, 0, nl * sizeof(double), h->stream));
+  CK(cudaMallocHost(&h->h_fl, FL_N * sizeof(int)));
+  CK(cudaMallocHost(&h->h_sc, SC_N * sizeof(double)));
+  for (auto &e : h->ev) CK(cudaEventCreate(&e));
+  return FP_OK;
+}
+
+// ------------------------------ building blocks -------------------------------------
+fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac, double *x,
+                       int mmax, const int *done) {
+  const int wpc = ntask >= 4 * h->num_sms ? 4 : (ntask >= 2 * h->num_sms ? 2 : 1);
+  const int grid = std::max(1, std::min(h->num_sms, (ntask + wpc - 1) / wpc));
+  CK(cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream));
+  CK(launch_band_solve(fp32, mmax, grid, wpc, h->stream, tasks, ntask, fac, x, h->counter, h->status, done));
+  return FP_OK;
+}
+
+fp_status solve_local(fp_handle *h, bool dirichlet, double *x, const int *done) {
+  const void *fac = dirichlet ? h->facD : h->facN;
+  const BandTask *tasks = dirichlet ? h->tasksD : h->tasksN;
+  return launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, x, h->mmax, done);
+}
+
+fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
+  const int nl = h->T.n_lambda;
+  if (!h->T.NF) {
+    if (out != v) CK(cudaMemcpyAsync(out, v, nl * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return FP_OK;
+  }
+  k_Gt<<<(h->T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->cy, fl);
+  k_gemv<<<(h->T.nH * 32 + 255) / 256, 256, 0, h->stream>>>(h->Hinv, h->cy, h->calpha, h->T.nH, fl);
+  k_Gcomb<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->calpha, v, -1.0, out, fl);
+  CKL();
+  return FP_OK;
+}
+
+// out = F v ; leaves K^+ B^T v in XB
+fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl) {
+  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, v, 1.0, h->XB, 1, fl);
+  CKL();
+  TRY(solve_local(h, false, h->XB, fl));
+  k_gather<<<(h->T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->XB, out, fl);
+  CKL();
+  return FP_OK;
+}
+
+// out = W B S B^T W v  (Eq. (3.5) with the scaling W)
+fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
+  const int nl = h->T.n_lambda;
+  const int ng = (int)h->T.wgrp_first.size();
+  if (h->P.precond == FP_PRECOND_NONE) {
+    if (out != v) CK(cudaMemcpyAsync(out, v, nl * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return FP_OK;
+  }
+  k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
+  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl);
+  k_halo<<<h->T.S, 256, 0, h->stream>>>(h->D, h->csr_val, h->XP, h->XY, fl);
+  CKL();
+  TRY(solve_local(h, true, h->XY, fl));
+  k_bnd_apply<<<h->T.S, 256, h->nbnd_max * sizeof(double), h->stream>>>(h->D, h->csr_val, h->XY, h->XP, fl);
+  k_gather<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, h->t2, fl);
+  k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, h->t2, out, fl);
+  CKL();
+  return FP_OK;
+}
+
+fp_status dot(fp_handle *h, const double *a, const double *b, int op, double *slot, const int *check) {
+  k_dot<<<RED_BLOCKS, 256, 0, h->stream>>>(a, b, h->T.n_lambda, h->partial, h->red_counter, h->sc, h->fl, op,
+                                           slot, check ? 1 : 0);
+  CKL();
+  return FP_OK;
+}
+
+fp_status lincomb(fp_handle *h, double *out, const double *x, double a, const double *y, double b, const int *fl) {
+  const int nl = h->T.n_lambda;
+  k_lincomb<<<(nl + 255) / 256, 256, 0, h->stream>>>(out, x, a, y, b, nl, fl);
+  CKL();
+  return FP_OK;
+}
+
+template <typename T>
+fp_status factor_T(fp_handle *h) {
+  Topology &Tp = h->T;
+  const size_t nf = (size_t)Tp.fac_off[Tp.S];
+  T *fN = nullptr, *fD = nullptr;
+  if (!h->facN) {
+    TRY(dalloc(h, &fN, nf));
+    TRY(dalloc(h, &fD, nf));
+    h->facN = fN; h->facD = fD;
+  }
+  fN = (T *)h->facN; fD = (T *)h->facD;
+  const bool f32 = sizeof(T) == 4;
+  CK(launch_csr_to_band(f32, h->D, h->csr_val, fN, 0, h->stream));
+  CK(launch_csr_to_band(f32, h->D, h->csr_val, fD, 1, h->stream));
+  int NB = 32;
+  while (NB > 4 && (size_t)NB * (h->ldmax + 1) * sizeof(T) > 200 * 1024) NB /= 2;
+  const size_t smem = (size_t)NB * (h->ldmax + 1) * sizeof(T);
+  CK(launch_band_factor(f32, h->tasksN, h->ntask, fN, NB, h->status, smem, h->stream));
+  CK(launch_band_factor(f32, h->tasksD, h->ntask, fD, NB, h->status, smem, h->stream));
+  return FP_OK;
+}
+
+fp_status factor_coarse(fp_handle *h) {
+  Topology &T = h->T;
+  if (!T.NF) return FP_OK;
+  if (!h->Hband) {
+    TRY(dalloc(h, &h->Hband, (size_t)T.nH * T.LDH));
+    TRY(dalloc(h, &h->Hinv, (size_t)T.nH * T.nH));
+  }
+  k_coarse_G<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->ga, h->gb);
+  CK(cudaMemsetAsync(h->Hband, 0, (size_t)T.nH * T.LDH * sizeof(double), h->stream));
+  k_coarse_GtG<<<(T.NF + 127) / 128, 128, 0, h->stream>>>(h->D, h->ga, h->gb, h->Hband);
+  CKL();
+  int NB = 32;
+  while (NB > 4 && (size_t)NB * (T.LDH + 1) * sizeof(double) > 200 * 1024) NB /= 2;
+  const size_t smem = (size_t)NB * (T.LDH + 1) * sizeof(double);
+  CK(launch_band_factor(false, h->taskH, 1, h->Hband, NB, h->status, smem, h->stream));
+  k_identity<<<1024, 256, 0, h->stream>>>(h->Hinv, T.nH);
+  CKL();
+  TRY(launch_solve(h, false, h->tasksHinv, T.nH, h->Hband, h->Hinv, h->mmaxH, nullptr));
+  return FP_OK;
+}
+
+fp_status check_status(fp_handle *h) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st == DS_ZERO_PIVOT) { h->err = "zero or non-finite pivot in a local LDL^T factorisation"; return FP_ERR_BREAKDOWN; }
+  if (st == DS_TIMEOUT) { h->err = "a bounded device wait gave up (TMA copy did not complete)"; return FP_ERR_TIMEOUT; }
+  if (st) { h->err = "device status " + std::to_string(st); return FP_ERR_BREAKDOWN; }
+  return FP_OK;
+}
+
+}  // namespace
+
+// ====================================== ABI ==========================================
+extern "C" {
+
+fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cuda_stream, fp_handle **out) {
+  if (!out) return FP_ERR_INVALID;
+  *out = nullptr;
+  fp_handle *h = new (std::nothrow) fp_handle();
+  if (!h) return FP_ERR_OOM;
+  if (!params || !mesh) { delete h; return FP_ERR_INVALID; }
+  h->P = *params;
+  if (!(h->P.lame_lambda > 0) || !(h->P.mu > 0) || !(h->P.c0 > 0) || !(h->P.tau > 0) || !(h->P.mu_f > 0) ||
+      !(h->P.alpha >= 0) || !(h->P.tol > 0) || h->P.max_it < 1 ||
+      (h->P.precision != FP_PREC_FP64 && h->P.precision != FP_PREC_MIXED) ||
+      (h->P.precond != FP_PRECOND_DIRICHLET && h->P.precond != FP_PRECOND_NONE)) {
+    g_create_err = "fp_create: invalid parameters";
+    delete h;
+    return FP_ERR_INVALID;
+  }
+  std::string err;
+  if (!build_topology(mesh, params, h->T, err)) {
+    g_create_err = "fp_create: " + err;
+    delete h;
+    return FP_ERR_INVALID;
+  }
+  if (params->perm) {
+    h->perm.assign(params->perm, params->perm + h->T.elem_off[h->T.S]);
+    for (double v : h->perm)
+      if (!(v > 0) || !std::isfinite(v)) { delete h; return FP_ERR_INVALID; }
+  }
+  h->P.perm = nullptr;
+  h->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return FP_ERR_CUDA; }
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  fp_status st = build_device(h);
+  if (st != FP_OK) { g_create_err = h->err; fp_destroy(h); return st; }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) { fp_destroy(h); return FP_ERR_CUDA; }
+  *out = h;
+  return FP_OK;
+}
+
+fp_status fp_assemble(fp_handle *h) {
+  if (!h) return FP_ERR_INVALID;
+  Topology &T = h->T;
+  CK(cudaMemsetAsync(h->csr_val, 0, T.csr_off[T.S] * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->fstat, 0, T.vec_off[T.S] * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->Zn, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->E0n, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
+  k_assemble<<<T.S, 256, 0, h->stream>>>(h->D, h->DP, h->csr_val, h->fstat, h->Zn, h->E0n);
+  CKL();
+  // initial state: R eta^0 = (eta_0, phi_i) (L2 projection), lambda^0 = 0
+  CK(cudaMemcpyAsync(h->Reta, h->E0n, T.pnode_off[T.S] * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemsetAsync(h->lam_prev, 0, std::max(T.n_lambda, 1) * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->U, 0, 2 * T.unode_off[T.S] * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->XI, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->ETA, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->PP, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->stage = 1;
+  h->step_n = 0;
+  return FP_OK;
+}
+
+fp_status fp_factor(fp_handle *h) {
+  if (!h) return FP_ERR_INVALID;
+  if (h->stage < 1) { h->err = "fp_factor before fp_assemble"; return FP_ERR_STATE; }
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  TRY(h->P.precision == FP_PREC_MIXED ? factor_T<float>(h) : factor_T<double>(h));
+  TRY(factor_coarse(h));
+  TRY(check_status(h));
+  h->stage = 2;
+  return FP_OK;
+}
+
+fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
+  if (!h) return FP_ERR_INVALID;
+  if (h->stage < 2) { h->err = "fp_step before fp_factor"; return FP_ERR_STATE; }
+  Topology &T = h->T;
+  const int nl = T.n_lambda;
+  const int n = h->step_n + 1;
+  const double t_now = n * h->P.tau;
+  cudaStream_t s = h->stream;
+  CK(cudaEventRecord(h->ev[0], s));
+  // flags and scalars
+  int hfl[FL_N] = {0, 0, 0, h->P.max_it, 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h->fl, hfl, sizeof hfl, cudaMemcpyHostToDevice, s));
+  const double tol2 = h->P.tol * h->P.tol;
+  CK(cudaMemcpyAsync(h->sc + SC_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+  // right-hand side, d = B K^+ f, e = R^T f
+  k_rhs<<<T.S, 256, 0, s>>>(h->D, h->DP, h->fstat, h->Zn, h->Reta, t_now, h->X2, h->ce);
+  CKL();
+  TRY(solve_local(h, false, h->X2, nullptr));
+  k_gather<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->X2, h->d, nullptr);
+  CKL();
+  // lambda_00 = G (G^T G)^{-1} e ; lambda_0 = lambda_00 + P lambda^{n-1}
+  if (T.NF) {
+    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->ce, h->calpha, T.nH, nullptr);
+    k_Gcomb<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->calpha, nullptr, 1.0, h->lam00, nullptr);
+    CKL();
+  } else {
+    CK(cudaMemsetAsync(h->lam00, 0, nl * sizeof(double), s));
+  }
+  TRY(apply_P(h, h->lam_prev, h->t1, h->fl_zero));
+  TRY(lincomb(h, h->lam, h->lam00, 1.0, h->t1, 1.0, nullptr));
+  // reference ||P(d - F lambda_00)||
+  if (T.NF) {
+    TRY(apply_F(h, h->lam00, h->t2, h->fl_zero));
+    TRY(lincomb(h, h->t2, h->d, 1.0, h->t2, -1.0, nullptr));
+    TRY(apply_P(h, h->t2, h->t2, h->fl_zero));
+    TRY(dot(h, h->t2, h->t2, OP_STORE, h->sc + SC_REF2, nullptr));
+  } else {
+    TRY(dot(h, h->d, h->d, OP_STORE, h->sc + SC_REF2, nullptr));
+  }
+  // r_0 = P(d - F lambda_0), z_0 = P M^{-1} r_0, p_0 = z_0
+  TRY(apply_F(h, h->lam, h->q, h->fl_zero));
+  TRY(lincomb(h, h->r, h->d, 1.0, h->q, -1.0, nullptr));
+  TRY(apply_P(h, h->r, h->r, h->fl_zero));
+  TRY(dot(h, h->r, h->r, OP_RNORM0, nullptr, nullptr));
+  TRY(apply_M(h, h->r, h->z, h->fl_zero));
+  TRY(apply_P(h, h->z, h->z, h->fl_zero));
+  CK(cudaMemcpyAsync(h->p, h->z, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TRY(dot(h, h->r, h->z, OP_RZ_INIT, nullptr, nullptr));
+  CK(cudaEventRecord(h->ev[1], s));
+  // Algorithm 1 loop; every kernel is a no-op once the device flag `done` is set
+  const int chunk = 8;
+  for (int it = 0; it < h->P.max_it; it += chunk) {
+    for (int c = 0; c < chunk; ++c) {
+      TRY(apply_F(h, h->p, h->q, h->fl));
+      TRY(apply_P(h, h->q, h->q, h->fl));
+      TRY(dot(h, h->p, h->q, OP_PQ, nullptr, h->fl));
+      k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
+      CKL();
+      TRY(apply_M(h, h->r, h->z, h->fl));
+      TRY(apply_P(h, h->z, h->z, h->fl));
+      TRY(dot(h, h->r, h->z, OP_RZ, nullptr, h->fl));
+      k_pcg_pupdate<<<(nl + 255) / 256, 256, 0, s>>>(h->p, h->z, nl, h->sc, h->fl);
+      CKL();
+    }
+    CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->h_fl[FL_DONE]) break;
+  }
+  CK(cudaEventRecord(h->ev[2], s));
+  // recovery: F lambda (leaves K^+ B^T lambda in XB), true residual, alpha, fields
+  TRY(apply_F(h, h->lam, h->t2, h->fl_zero));
+  TRY(lincomb(h, h->t1, h->d, 1.0, h->t2, -1.0, nullptr));
+  TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
+  TRY(dot(h, h->t1, h->t1, OP_STORE, h->sc + SC_TRUE2, nullptr));
+  if (T.NF) {
+    TRY(lincomb(h, h->t1, h->t2, 1.0, h->d, -1.0, nullptr));
+    k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr);
+    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->cy, h->calpha, T.nH, nullptr);
+    CKL();
+  }
+  k_recover<<<T.S, 256, 0, s>>>(h->D, h->DP, h->X2, h->XB, h->calpha, h->U, h->XI, h->ETA, h->PP, h->Reta);
+  CKL();
+  CK(cudaMemcpyAsync(h->lam_prev, h->lam, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaEventRecord(h->ev[3], s));
+  CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms01 = 0, ms12 = 0, ms23 = 0;
+  cudaEventElapsedTime(&ms01, h->ev[0], h->ev[1]);
+  cudaEventElapsedTime(&ms12, h->ev[1], h->ev[2]);
+  cudaEventElapsedTime(&ms23, h->ev[2], h->ev[3]);
+  h->last_ms[0] = ms01; h->last_ms[1] = ms12; h->last_ms[2] = ms23; h->last_ms[3] = 0;
+  h->step_n = n;
+  const double ref2 = h->h_sc[SC_REF2];
+  if (stats) {
+    stats->step = n;
+    stats->iterations = h->h_fl[FL_ITER];
+    stats->rel_residual = ref2 > 0 ? std::sqrt(h->h_sc[SC_RNORM2] / ref2) : 0.0;
+    stats->true_rel_residual = ref2 > 0 ? std::sqrt(h->h_sc[SC_TRUE2] / ref2) : 0.0;
+  }
+  fp_status st = check_status(h);
+  if (st) return st;
+  if (h->h_fl[FL_STATUS] == DS_BREAKDOWN) { h->err = "PCG breakdown (p^T F p = 0 or non-finite)"; return FP_ERR_BREAKDOWN; }
+  if (h->h_fl[FL_STATUS]) { h->err = "non-finite values in PCG"; return FP_ERR_BREAKDOWN; }
+  if (!(h->h_sc[SC_RNORM2] <= tol2 * ref2)) { h->err = "PCG did not converge within max_it"; return FP_ERR_NOT_CONVERGED; }
+  return FP_OK;
+}
+
+fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last) {
+  for (int i = 0; i < n_steps; ++i) {
+    fp_status st = fp_step(h, last);
+    if (st) return st;
+  }
+  return FP_OK;
+}
+
+fp_status fp_get_sizes(const fp_handle *h, fp_sizes *o) {
+  if (!h || !o) return FP_ERR_INVALID;
+  const Topology &T = h->T;
+  o->nsub = T.S; o->n_floating = T.NF; o->n_lambda = T.n_lambda; o->n_lambda_p = T.n_lambda_p;
+  long long nd = 0;
+  int bmax = 0;
+  for (int s = 0; s < T.S; ++s) { nd += T.tpl[T.sub_tpl[s]].n; bmax = std::max(bmax, T.tpl[T.sub_tpl[s]].b); }
+  o->n_dofs = nd;
+  o->n_unode_total = T.unode_off[T.S];
+  o->n_pnode_total = T.pnode_off[T.S];
+  o->factor_bytes = 2LL * T.fac_off[T.S] * (h->P.precision == FP_PREC_MIXED ? 4 : 8);
+  o->max_half_band = bmax;
+  return FP_OK;
+}
+
+static fp_status copy_out(fp_handle *h, void *dst, const void *src, size_t bytes, int on_device) {
+  if (!dst) return FP_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FP_OK;
+}
+
+fp_status fp_get_lambda(const fp_handle *hc, double *dst, int on_device) {
+  fp_handle *h = const_cast<fp_handle *>(hc);
+  if (!h || !dst) return FP_ERR_INVALID;
+  return copy_out(h, dst, h->lam_prev, h->T.n_lambda * sizeof(double), on_device);
+}
+
+fp_status fp_get_lambda_keys(const fp_handle *h, int *keys) {
+  if (!h || !keys) return FP_ERR_INVALID;
+  std::memcpy(keys, h->T.lam_key.data(), h->T.lam_key.size() * sizeof(int));
+  return FP_OK;
+}
+
+fp_status fp_get_fields(const fp_handle *hc, double *u, double *xi, double *eta, double *p, int on_device) {
+  fp_handle *h = const_cast<fp_handle *>(hc);
+  if (!h) return FP_ERR_INVALID;
+  const Topology &T = h->T;
+  TRY(copy_out(h, u, h->U, 2 * T.unode_off[T.S] * sizeof(double), on_device));
+  TRY(copy_out(h, xi, h->XI, T.pnode_off[T.S] * sizeof(double), on_device));
+  TRY(copy_out(h, eta, h->ETA, T.pnode_off[T.S] * sizeof(double), on_device));
+  TRY(copy_out(h, p, h->PP, T.pnode_off[T.S] * sizeof(double), on_device));
+  return FP_OK;
+}
+
+static fp_status apply_op_abi(fp_handle *h, const double *v, double *out, int on_device, int which) {
+  if (!h || !v || !out) return FP_ERR_INVALID;
+  if (h->stage < 2) { h->err = "operator before fp_factor"; return FP_ERR_STATE; }
+  const size_t bytes = h->T.n_lambda * sizeof(double);
+  double *vin = h->p;  // scratch copy of the input
+  CK(cudaMemcpyAsync(vin, v, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  fp_status st = which == 0 ? apply_F(h, vin, h->q, h->fl_zero)
+                 : which == 1 ? apply_M(h, vin, h->q, h->fl_zero)
+                              : apply_P(h, vin, h->q, h->fl_zero);
+  if (st) return st;
+  TRY(copy_out(h, out, h->q, bytes, on_device));
+  return check_status(h);
+}
+
+fp_status fp_apply_F(fp_handle *h, const double *v, double *out, int on_device) { return apply_op_abi(h, v, out, on_device, 0); }
+fp_status fp_apply_precond(fp_handle *h, const double *v, double *out, int on_device) { return apply_op_abi(h, v, out, on_device, 1); }
+fp_status fp_apply_projection(fp_handle *h, const double *v, double *out, int on_device) { return apply_op_abi(h, v, out, on_device, 2); }
+
+fp_status fp_get_dof_map(const fp_handle *h, int s, int *field, int *node, int *n_out) {
+  if (!h || s < 0 || s >= h->T.S) return FP_ERR_INVALID;
+  const Template &t = h->T.tpl[h->T.sub_tpl[s]];
+  if (n_out) *n_out = t.n;
+  if (field) std::memcpy(field, t.dof_field.data(), t.n * sizeof(int));
+  if (node) std::memcpy(node, t.dof_node.data(), t.n * sizeof(int));
+  return FP_OK;
+}
+
+fp_status fp_get_local_matrix(const fp_handle *hc, int s, double *dense) {
+  fp_handle *h = const_cast<fp_handle *>(hc);
+  if (!h || !dense || s < 0 || s >= h->T.S) return FP_ERR_INVALID;
+  if (h->stage < 1) { h->err = "before fp_assemble"; return FP_ERR_STATE; }
+  const Template &t = h->T.tpl[h->T.sub_tpl[s]];
+  double *band = nullptr, *out = nullptr;
+  CK(cudaMalloc(&band, (size_t)t.n * t.LD * sizeof(double)));
+  CK(cudaMalloc(&out, (size_t)t.n * t.n * sizeof(double)));
+  // rebuild the plain (Neumann, no identity rows) band of s from the CSR values
+  std::vector<double> hv(t.csr_col.size());
+  cudaMemcpy(hv.data(), h->csr_val + h->T.csr_off[s], hv.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  std::vector<double> hb((size_t)t.n * t.LD, 0.0);
+  for (int r = 0; r < t.n; ++r)
+    for (int e = t.csr_ptr[r]; e < t.csr_ptr[r + 1]; ++e) {
+      const int c = t.csr_col[e];
+      if (c <= r) hb[(size_t)c * t.LD + r % t.LD] = hv[e];
+    }
+  cudaMemcpy(band, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice);
+  launch_band_to_dense(band, t.n, t.LD, t.b, out, nullptr);
+  cudaError_t e = cudaMemcpy(dense, out, (size_t)t.n * t.n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(band);
+  cudaFree(out);
+  if (e != cudaSuccess) { h->err = cudaGetErrorString(e); return FP_ERR_CUDA; }
+  return FP_OK;
+}
+
+fp_status fp_get_step_timing(const fp_handle *h, double *ms4) {
+  if (!h || !ms4) return FP_ERR_INVALID;
+  for (int i = 0; i < 4; ++i) ms4[i] = h->last_ms[i];
+  return FP_OK;
+}
+
+const char *fp_last_error(const fp_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+void fp_destroy(fp_handle *h) {
+  if (!h) return;
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->h_fl) cudaFreeHost(h->h_fl);
+  if (h->h_sc) cudaFreeHost(h->h_sc);
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,403 @@
+// Batched banded LDL^T factorisation and solves for the local systems K_s (Sec. 3.2:
+// K_A needs K_s^{-1} applied to interface data, no nested iteration) and for the coarse
+// matrix G^T G.
+//
+// Storage ("cyclic column layout"): a band matrix of order n and half bandwidth b is stored
+// as n columns of LD >= b + 1 slots (LD a multiple of 32).  Column j keeps entry (r, j),
+// j <= r <= j + b, in slot r mod LD; the other slots are zero.  After factorisation slot
+// j mod LD holds 1/d_j and the other slots the unit-lower factor L.  With this layout a
+// warp solving one system keeps the moving window of pending rows in registers indexed by
+// slot, so the window never moves between lanes: lane l owns slots l, l+32, ...
+//
+// Factorisation: right-looking, panels of NB columns staged in shared memory, trailing
+// update of the (b x b) triangle in 4x4 register tiles.  One CTA per matrix.
+// Solve: one warp per system (dynamic work queue, tasks pre-sorted by cost), forward
+// sweep (axpy form), diagonal, backward sweep (dot form with warp reductions).  Factor
+// columns are streamed through a per-warp ring of shared-memory stages filled by TMA bulk
+// copies (cp.async.bulk + mbarrier), with bounded waits that report DS_TIMEOUT.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace fp {
+
+// ============================ factorisation ============================================
+template <typename T>
+__global__ void __launch_bounds__(256) k_band_factor(const BandTask *tasks, int ntask, T *base, int NB,
+                                                     int *status) {
+  const int task = blockIdx.x;
+  if (task >= ntask) return;
+  const BandTask tk = tasks[task];
+  T *A = base + tk.fac_off;
+  const int n = tk.n, LD = tk.LD, b = tk.b;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *pan = reinterpret_cast<T *>(smem_raw);
+  T *dpan = pan + (size_t)NB * LD;
+  for (int J = 0; J < n; J += NB) {
+    const int nbw = min(NB, n - J);
+    for (int e = threadIdx.x; e < nbw * LD; e += blockDim.x) pan[e] = A[(long long)J * LD + e];
+    __syncthreads();
+    for (int c = 0; c < nbw; ++c) {
+      const int j = J + c;
+      const T d = pan[c * LD + j % LD];
+      const T dinv = T(1) / d;
+      if (threadIdx.x == 0) {
+        dpan[c] = d;
+        if (!(d != T(0)) || !isfinite((double)d)) set_status(status, DS_ZERO_PIVOT);
+      }
+      const int rmax = min(n - 1, j + b);
+      const int ncols = nbw - c - 1;
+      const int span = b + 1;
+      for (int idx = threadIdx.x; idx < ncols * span; idx += blockDim.x) {
+        const int c2 = c + 1 + idx / span;
+        const int r = J + c2 + idx % span;
+        if (r > rmax) continue;
+        const T lrj = pan[c * LD + r % LD] * dinv;
+        const T a_c2j = pan[c * LD + (J + c2) % LD];
+        pan[c2 * LD + r % LD] -= lrj * a_c2j;
+      }
+      __syncthreads();
+      for (int r = j + 1 + threadIdx.x; r <= rmax; r += blockDim.x) pan[c * LD + r % LD] *= dinv;
+      if (threadIdx.x == 0) pan[c * LD + j % LD] = dinv;
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nbw * LD; e += blockDim.x) A[(long long)J * LD + e] = pan[e];
+    // trailing update of rows/columns [T0, T1)
+    const int T0 = J + nbw, T1 = min(n, J + nbw + b);
+    const int m = T1 - T0;
+    if (m > 0) {
+      const int nt = (m + 3) / 4;
+      const int npairs = nt * (nt + 1) / 2;
+      for (int pidx = threadIdx.x; pidx < npairs; pidx += blockDim.x) {
+        int ti = (int)((sqrt(8.0 * pidx + 1.0) - 1.0) * 0.5);
+        while (ti * (ti + 1) / 2 > pidx) --ti;
+        while ((ti + 1) * (ti + 2) / 2 <= pidx) ++ti;
+        const int tj = pidx - ti * (ti + 1) / 2;
+        const int i0 = T0 + 4 * ti, j0 = T0 + 4 * tj;
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[a][q] = T(0);
+        for (int c = 0; c < nbw; ++c) {
+          const int jc = J + c;
+          const T dc = dpan[c];
+          T li[4], lj[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int r = i0 + q;
+            li[q] = (r < T1 && r - jc <= b) ? pan[c * LD + r % LD] : T(0);
+            const int r2 = j0 + q;
+            lj[q] = (r2 < T1 && r2 - jc <= b) ? pan[c * LD + r2 % LD] * dc : T(0);
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] += li[a] * lj[q];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = i0 + a, jj = j0 + q;
+            if (i < T1 && jj < T1 && i >= jj) A[(long long)jj * LD + i % LD] -= acc[a][q];
+          }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template __global__ void k_band_factor<double>(const BandTask *, int, double *, int, int *);
+template __global__ void k_band_factor<float>(const BandTask *, int, float *, int, int *);
+
+// ============================ TMA ring helpers ==========================================
+namespace {
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^31 SM cycles (about a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+}  // namespace
+
+constexpr int SOLVE_STAGES = 3;
+constexpr int CHUNK_BYTES = 16384;
+
+// Per-warp ring of SOLVE_STAGES stages.  Requests are numbered per warp (seq); request q
+// lives in stage q % S and completes phase (q / S) & 1 of that stage's mbarrier.
+struct Ring {
+  unsigned char *buf;
+  uint64_t *bar;
+  uint32_t seq0;  // global number of the current task's request 0
+};
+
+template <typename T>
+struct TaskStream {
+  const T *fac;
+  int n, LD, C, nc;
+  __device__ __forceinline__ int chunk_of_req(int r) const { return r < nc ? r : 2 * nc - 1 - r; }
+  __device__ __forceinline__ void issue(const Ring &rg, int r) const {
+    const int c = chunk_of_req(r);
+    const int c0 = c * C;
+    const int cols = min(C, n - c0);
+    const uint32_t bytes = (uint32_t)cols * LD * sizeof(T);
+    const uint32_t q = rg.seq0 + r;
+    const int st = q % SOLVE_STAGES;
+    mbar_expect_tx(&rg.bar[st], bytes);
+    bulk_g2s(rg.buf + (size_t)st * CHUNK_BYTES, fac + (long long)c0 * LD, bytes, &rg.bar[st]);
+  }
+};
+
+template <typename T, int MMAX>
+__global__ void __launch_bounds__(128) k_band_solve(const BandTask *tasks, int ntask, const T *fbase,
+                                                    double *xbase, int *counter, int *status,
+                                                    const int *done) {
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  extern __shared__ __align__(128) unsigned char smem[];
+  Ring rg;
+  rg.buf = smem + (size_t)warp * SOLVE_STAGES * CHUNK_BYTES;
+  rg.bar = reinterpret_cast<uint64_t *>(smem + (size_t)nwarps * SOLVE_STAGES * CHUNK_BYTES) + warp * SOLVE_STAGES;
+  if (lane == 0)
+    for (int st = 0; st < SOLVE_STAGES; ++st) mbar_init(&rg.bar[st], 1);
+  fence_mbar_init();
+  __syncwarp();
+  rg.seq0 = 0;
+  bool abort = false;
+  uint32_t inflight_lo = 0, inflight_hi = 0;  // requests [lo, hi) issued and not consumed
+  while (!abort) {
+    int task = 0;
+    if (lane == 0) task = atomicAdd(counter, 1);
+    task = __shfl_sync(FULL, task, 0);
+    if (task >= ntask) break;
+    const BandTask tk = tasks[task];
+    TaskStream<T> ts;
+    ts.fac = fbase + tk.fac_off;
+    ts.n = tk.n;
+    ts.LD = tk.LD;
+    ts.C = max(1, CHUNK_BYTES / (int)(tk.LD * sizeof(T)));
+    ts.nc = (ts.n + ts.C - 1) / ts.C;
+    double *x = xbase + tk.x_off;
+    const int n = ts.n, LD = ts.LD, M = LD / 32, C = ts.C;
+    const int R = 2 * ts.nc;
+    if (lane == 0)
+      for (int r = 0; r < min(SOLVE_STAGES, R); ++r) ts.issue(rg, r);
+    inflight_lo = rg.seq0;
+    inflight_hi = rg.seq0 + min(SOLVE_STAGES, R);
+    // wait for request r: returns false on timeout (uniform over the warp)
+    auto wait_req = [&](int r) -> bool {
+      const uint32_t q = rg.seq0 + r;
+      const bool ok = mbar_wait(&rg.bar[q % SOLVE_STAGES], (q / SOLVE_STAGES) & 1);
+      return __all_sync(FULL, ok);
+    };
+    auto release_req = [&](int r) {
+      __syncwarp();
+      inflight_lo = rg.seq0 + r + 1;
+      if (r + SOLVE_STAGES < R) {
+        if (lane == 0) {
+          fence_proxy_async();
+          ts.issue(rg, r + SOLVE_STAGES);
+        }
+        inflight_hi = rg.seq0 + r + SOLVE_STAGES + 1;
+      }
+    };
+    const int nblk = (n + 31) / 32;
+    // ---------------- forward sweep: L y = x, z = D^{-1} y --------------------------
+    T w[MMAX];
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m) {
+      const int row = m * 32 + lane;
+      w[m] = (m < M && row < n) ? T(x[row]) : T(0);
+    }
+    int cur = -1, cstart = 0, cend = 0;
+    const T *cb = nullptr;
+    for (int q = 0; q < nblk && !abort; ++q) {
+      const int j0 = q * 32;
+      const int g = q % M;
+      int offs[MMAX];
+#pragma unroll
+      for (int m = 0; m < MMAX; ++m) offs[m] = (m < M) ? ((g + m) % M) * 32 + lane : 0;
+      const int rr = j0 + LD + lane;
+      const T refill = rr < n ? T(x[rr]) : T(0);
+      T zout = T(0);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int j = j0 + i;
+        if (j >= n) break;
+        if (j >= cend) {
+          if (cur >= 0) release_req(cur);
+          cur = j / C;
+          if (!wait_req(cur)) { abort = true; break; }
+          cb = reinterpret_cast<const T *>(rg.buf + (size_t)((rg.seq0 + cur) % SOLVE_STAGES) * CHUNK_BYTES);
+          cstart = cur * C;
+          cend = min(n, cstart + C);
+        }
+        const T *col = cb + (size_t)(j - cstart) * LD;
+        const T yj = __shfl_sync(FULL, w[0], i);
+        const T c0 = col[offs[0]];
+        if (lane == i) zout = yj * c0;
+        w[0] -= c0 * yj;
+#pragma unroll
+        for (int m = 1; m < MMAX; ++m)
+          if (m < M) w[m] -= col[offs[m]] * yj;
+        if (lane == i) w[0] = refill;
+      }
+      if (abort) break;
+      if (j0 + lane < n) x[j0 + lane] = double(zout);
+      const T t0 = w[0];
+#pragma unroll
+      for (int m = 0; m < MMAX; ++m) {
+        if (m < M - 1) w[m] = w[(m + 1 < MMAX) ? m + 1 : m];
+        else if (m == M - 1) w[m] = t0;
+      }
+    }
+    if (abort) break;
+    release_req(cur);
+    // ---------------- backward sweep: L^T x = z --------------------------------------
+    T xw[MMAX];
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m) xw[m] = T(0);
+    int curb = -1;
+    cstart = n;
+    for (int q = nblk - 1; q >= 0 && !abort; --q) {
+      const int j0 = q * 32;
+      const int g = q % M;
+      int offs[MMAX];
+#pragma unroll
+      for (int m = 0; m < MMAX; ++m) offs[m] = (m < M) ? ((g + m) % M) * 32 + lane : 0;
+      const T zin = (j0 + lane < n) ? T(x[j0 + lane]) : T(0);
+      T xout = T(0);
+#pragma unroll
+      for (int i = 31; i >= 0; --i) {
+        const int j = j0 + i;
+        if (j >= n) continue;
+        if (j < cstart) {
+          if (curb >= 0) release_req(curb);
+          const int c = j / C;
+          curb = 2 * ts.nc - 1 - c;
+          if (!wait_req(curb)) { abort = true; break; }
+          cb = reinterpret_cast<const T *>(rg.buf + (size_t)((rg.seq0 + curb) % SOLVE_STAGES) * CHUNK_BYTES);
+          cstart = c * C;
+        }
+        const T *col = cb + (size_t)(j - cstart) * LD;
+        T part = (lane == i) ? T(0) : col[offs[0]] * xw[0];
+#pragma unroll
+        for (int m = 1; m < MMAX; ++m)
+          if (m < M) part += col[offs[m]] * xw[m];
+        part = warp_sum(part);
+        if (lane == i) {
+          xw[0] = zin - part;
+          xout = xw[0];
+        }
+      }
+      if (abort) break;
+      if (j0 + lane < n) x[j0 + lane] = double(xout);
+      T tl = xw[0];
+#pragma unroll
+      for (int m = 1; m < MMAX; ++m)
+        if (m == M - 1) tl = xw[m];
+#pragma unroll
+      for (int m = MMAX - 1; m >= 1; --m)
+        if (m < M) xw[m] = xw[m - 1];
+      xw[0] = tl;
+    }
+    if (abort) break;
+    release_req(curb);
+    rg.seq0 += R;
+    inflight_lo = inflight_hi = rg.seq0;
+  }
+  if (abort) {
+    if (lane == 0) set_status(status, DS_TIMEOUT);
+    // wait (bounded) for copies still in flight before the CTA may exit
+    for (uint32_t q = inflight_lo; q < inflight_hi; ++q) mbar_wait(&rg.bar[q % SOLVE_STAGES], (q / SOLVE_STAGES) & 1);
+  }
+}
+
+#define FP_SOLVE_INST(T, MM)                                                                           \
+  template __global__ void k_band_solve<T, MM>(const BandTask *, int, const T *, double *, int *, int *, \
+                                               const int *);
+FP_SOLVE_INST(double, 4)
+FP_SOLVE_INST(double, 8)
+FP_SOLVE_INST(double, 12)
+FP_SOLVE_INST(double, 16)
+FP_SOLVE_INST(float, 4)
+FP_SOLVE_INST(float, 8)
+FP_SOLVE_INST(float, 12)
+FP_SOLVE_INST(float, 16)
+
+size_t solve_smem_bytes(int warps_per_cta) {
+  return (size_t)warps_per_cta * SOLVE_STAGES * CHUNK_BYTES + (size_t)warps_per_cta * SOLVE_STAGES * 8;
+}
+
+// Host launchers (template kernel stubs are not visible across translation units).
+cudaError_t launch_band_factor(bool fp32, const BandTask *tasks, int ntask, void *base, int NB, int *status,
+                               size_t smem, cudaStream_t stream) {
+  cudaError_t e;
+  if (fp32) {
+    e = cudaFuncSetAttribute(k_band_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_band_factor<float><<<ntask, 256, smem, stream>>>(tasks, ntask, (float *)base, NB, status);
+  } else {
+    e = cudaFuncSetAttribute(k_band_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_band_factor<double><<<ntask, 256, smem, stream>>>(tasks, ntask, (double *)base, NB, status);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_solve_T(int mmax, int grid, int wpc, cudaStream_t stream, const BandTask *tasks,
+                                  int ntask, const T *fac, double *x, int *counter, int *status, const int *done) {
+  void (*kern)(const BandTask *, int, const T *, double *, int *, int *, const int *) = nullptr;
+  switch (mmax) {
+    case 4: kern = k_band_solve<T, 4>; break;
+    case 8: kern = k_band_solve<T, 8>; break;
+    case 12: kern = k_band_solve<T, 12>; break;
+    default: kern = k_band_solve<T, 16>; break;
+  }
+  const size_t smem = solve_smem_bytes(wpc);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 32 * wpc, smem, stream>>>(tasks, ntask, fac, x, counter, status, done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_solve(bool fp32, int mmax, int grid, int wpc, cudaStream_t stream, const BandTask *tasks,
+                              int ntask, const void *fac, double *x, int *counter, int *status, const int *done) {
+  if (fp32) return launch_solve_T<float>(mmax, grid, wpc, stream, tasks, ntask, (const float *)fac, x, counter, status, done);
+  return launch_solve_T<double>(mmax, grid, wpc, stream, tasks, ntask, (const double *)fac, x, counter, status, done);
+}
+
+}  // namespace fp

@@ -1,0 +1,82 @@
+// Device-side views of the topology and small helpers shared by the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fp {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Template (per subdomain shape) data, flattened.
+struct DevTpl {
+  int n, b, LD, k, poro, nx, ny, nux, nuy, npx, npy, ndl, floating;
+  int fixed0, fixed1, fixed2;
+  int nbnd, nhalo, nnz;
+  long long udof, xidof, pdof;          // offsets into the int pool
+  long long dof_field, dof_node;
+  long long csr_ptr, csr_col;
+  long long bnd, is_bnd;
+  long long halo_ptr, halo_row, halo_ent;
+  long long elem_dofs;
+};
+
+// Everything the kernels need about the partition, by pointer.
+struct DevTopo {
+  int S, NF, nlam, nH, bH, LDH, k, nsx, nsy;
+  const DevTpl *tpl;
+  const int *pool;                  // integer pool for template arrays
+  const int *sub_tpl;
+  const double *sub_x0, *sub_y0, *sub_hx, *sub_hy;
+  const long long *vec_off, *fac_off, *csr_off, *unode_off, *pnode_off, *elem_off, *bsc_off;
+  const int *sub_I0, *sub_J0;
+  // interface
+  const int *lam_sa, *lam_da, *lam_sb, *lam_db, *lam_kind;
+  const int *wgrp_first, *wgrp_size;
+  int nwgrp;
+  const int *bsc_row;
+  const int8_t *bsc_sign;
+  // coarse
+  const int *sub_float, *float_sub, *float_rows_ptr, *float_rows;
+  const int *lam_fa, *lam_fb;        // floating index of s_a / s_b or -1
+  const double *lam_ga, *lam_gb;     // [3 * nlam] G row entries for s_a / s_b
+};
+
+// Physical parameters used inside kernels.
+struct DevParams {
+  double lam, mu, alpha, c0, perm_k, mu_f, tau, q_omega;
+  int source, src_sub, src_node;
+  const double *perm;               // per element or null
+};
+
+// A batched banded solve/factor task.
+struct BandTask {
+  long long fac_off;   // element offset of the factor
+  long long x_off;     // element offset of the vector
+  int n, LD, b, pad;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// PCG state kept on the device: scalar slots, integer flags, reduction finalisers
+enum ScSlot { SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RNORM2, SC_REF2, SC_TOL2, SC_TMP, SC_TRUE2, SC_N = 16 };
+enum FlSlot { FL_DONE = 0, FL_ITER, FL_STATUS, FL_MAXIT, FL_N = 8 };
+enum RedOp { OP_STORE = 0, OP_PQ = 1, OP_RZ_INIT = 2, OP_RZ = 3, OP_RNORM = 4, OP_RNORM0 = 5 };
+constexpr int RED_BLOCKS = 296;  // fixed grid of the two-stage reductions (deterministic)
+
+// status codes written by kernels (first error wins)
+enum DevStatus { DS_OK = 0, DS_ZERO_PIVOT = 1, DS_TIMEOUT = 2, DS_BREAKDOWN = 3, DS_NONFINITE = 4 };
+
+__device__ __forceinline__ void set_status(int *st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+}  // namespace fp

@@ -1,0 +1,406 @@
+// FETI interface kernels (Sec. 3): jump operator B / B^T, the scaling W = (B B^T)^{-1},
+// the sparse parts of the Dirichlet preconditioner (Eq. (3.5)), the FETI-1 coarse
+// projection P = I - G (G^T G)^{-1} G^T, per-step right-hand side and recovery, and the
+// reductions and vector updates of Algorithm 1 with all scalars kept on the device.
+// Every reduction has a fixed order (per-block tree, then the partials in block order), so
+// results are bitwise reproducible run to run.
+#include <cmath>
+
+#include "device.cuh"
+
+namespace fp {
+
+// ------------------------------------------------------------------------------------
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// last-block finalisation of a two-stage reduction; returns true in the finishing thread
+__device__ bool finish_reduction(double local, double *partial, unsigned *counter, double &total) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const double bsum = block_sum(local, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = bsum;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) t += ((volatile double *)partial)[i];
+    total = t;
+    *counter = 0u;
+    return true;
+  }
+  return false;
+}
+
+__device__ void apply_op(int op, double v, double *sc, int *fl) {
+  switch (op) {
+    case OP_STORE:
+      sc[SC_TMP] = v;
+      break;
+    case OP_PQ:
+      sc[SC_PQ] = v;
+      if (!(v != 0.0) || !isfinite(v)) {
+        fl[FL_STATUS] = DS_BREAKDOWN;
+        fl[FL_DONE] = 1;
+      } else {
+        sc[SC_ALPHA] = sc[SC_RZ] / v;
+      }
+      break;
+    case OP_RZ_INIT:
+      sc[SC_RZ] = v;
+      break;
+    case OP_RZ:
+      if (!isfinite(v)) { fl[FL_STATUS] = DS_NONFINITE; fl[FL_DONE] = 1; }
+      sc[SC_BETA] = v / sc[SC_RZ];
+      sc[SC_RZ] = v;
+      break;
+    case OP_RNORM0:
+      sc[SC_RNORM2] = v;
+      if (!isfinite(v)) { fl[FL_STATUS] = DS_NONFINITE; fl[FL_DONE] = 1; }
+      else if (v <= sc[SC_TOL2] * sc[SC_REF2]) fl[FL_DONE] = 1;
+      break;
+    case OP_RNORM:
+      sc[SC_RNORM2] = v;
+      fl[FL_ITER] += 1;
+      if (!isfinite(v)) { fl[FL_STATUS] = DS_NONFINITE; fl[FL_DONE] = 1; }
+      else if (v <= sc[SC_TOL2] * sc[SC_REF2]) fl[FL_DONE] = 1;
+      else if (fl[FL_ITER] >= fl[FL_MAXIT]) fl[FL_DONE] = 1;
+      break;
+  }
+}
+
+// dot(a, b) -> op.  If out_slot is given the raw value is also stored there.
+__global__ void k_dot(const double *a, const double *b, long long n, double *partial, unsigned *counter,
+                      double *sc, int *fl, int op, double *out_slot, int check_done) {
+  if (check_done && fl[FL_DONE]) return;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  double tot;
+  if (finish_reduction(s, partial, counter, tot)) {
+    if (out_slot) *out_slot = tot;
+    apply_op(op, tot, sc, fl);
+  }
+}
+
+// lambda += alpha p; r -= alpha q; then ||r||^2 -> stop test (Algorithm 1, lines 5-6)
+__global__ void k_pcg_update(double *lam, double *r, const double *p, const double *q, long long n,
+                             double *partial, unsigned *counter, double *sc, int *fl) {
+  if (fl[FL_DONE]) return;
+  const double alpha = sc[SC_ALPHA];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    lam[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  double tot;
+  if (finish_reduction(s, partial, counter, tot)) apply_op(OP_RNORM, tot, sc, fl);
+}
+
+// p = z + beta p (Algorithm 1, line 9)
+__global__ void k_pcg_pupdate(double *p, const double *z, long long n, const double *sc, const int *fl) {
+  if (fl[FL_DONE]) return;
+  const double beta = sc[SC_BETA];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// out = a x + b y  (host scalars; y may be null)
+__global__ void k_lincomb(double *out, const double *x, double a, const double *y, double b, long long n,
+                          const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+// ---------------------------------- jump operator -----------------------------------
+// Local vectors x_s = scale * B_s^T v on the dofs touched by B_s, zero elsewhere.
+// skip_fixed: leave the fixed dofs of floating subdomains at zero (K^+ convention).
+__global__ void k_scatter(DevTopo D, const double *v, double scale, double *xloc, int skip_fixed, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  double *x = xloc + D.vec_off[s];
+  for (int d = threadIdx.x; d < t.n; d += blockDim.x) x[d] = 0.0;
+  __syncthreads();
+  const int *bnd = D.pool + t.bnd;
+  const long long b0 = D.bsc_off[s];
+  for (int q = threadIdx.x; q < t.nbnd; q += blockDim.x) {
+    const int d = bnd[q];
+    if (skip_fixed && t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2)) continue;
+    double acc = 0.0;
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+      const int r = D.bsc_row[3 * (b0 + q) + z];
+      if (r >= 0) acc += D.bsc_sign[3 * (b0 + q) + z] * v[r];
+    }
+    x[d] = scale * acc;
+  }
+}
+
+// out[r] = x_{s_a}[d_a] - x_{s_b}[d_b]
+__global__ void k_gather(DevTopo D, const double *xloc, double *out, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= D.nlam) return;
+  out[r] = xloc[D.vec_off[D.lam_sa[r]] + D.lam_da[r]] - xloc[D.vec_off[D.lam_sb[r]] + D.lam_db[r]];
+}
+
+// out = W v, W = (B B^T)^{-1}: per node component a chain of m-1 <= 3 rows whose B B^T is
+// tridiag(-1, 2, -1); its inverse in closed form.
+__global__ void k_wscale(DevTopo D, const double *v, double *out, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= D.nwgrp) return;
+  const int f = D.wgrp_first[gidx], m = D.wgrp_size[gidx];
+  if (m == 1) {
+    out[f] = 0.5 * v[f];
+  } else if (m == 2) {
+    const double a = v[f], b = v[f + 1];
+    out[f] = (2 * a + b) / 3.0;
+    out[f + 1] = (a + 2 * b) / 3.0;
+  } else {
+    const double a = v[f], b = v[f + 1], c = v[f + 2];
+    out[f] = (3 * a + 2 * b + c) / 4.0;
+    out[f + 1] = (2 * a + 4 * b + 2 * c) / 4.0;
+    out[f + 2] = (a + 2 * b + 3 * c) / 4.0;
+  }
+}
+
+// ------------------------------ Dirichlet preconditioner -----------------------------
+// y_s = -K_{I b} xb_s on the halo rows (rows outside b coupled to b), zero elsewhere.
+__global__ void k_halo(DevTopo D, const double *csr_val, const double *xb, double *y, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const double *xs = xb + D.vec_off[s];
+  double *ys = y + D.vec_off[s];
+  for (int d = threadIdx.x; d < t.n; d += blockDim.x) ys[d] = 0.0;
+  __syncthreads();
+  const int *hp = D.pool + t.halo_ptr, *hr = D.pool + t.halo_row, *he = D.pool + t.halo_ent;
+  const int *ccol = D.pool + t.csr_col;
+  const double *val = csr_val + D.csr_off[s];
+  for (int h = threadIdx.x; h < t.nhalo; h += blockDim.x) {
+    double acc = 0.0;
+    for (int e = hp[h]; e < hp[h + 1]; ++e) acc += val[he[e]] * xs[ccol[he[e]]];
+    ys[hr[h]] = -acc;
+  }
+}
+
+// z_b = K_{b .} (y + xb) on the rows of b (the Schur complement S_s xb, since y solves the
+// Dirichlet problem); written back into xb at the rows of b.
+__global__ void k_bnd_apply(DevTopo D, const double *csr_val, const double *y, double *xb, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  extern __shared__ double zsh[];
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const double *ys = y + D.vec_off[s];
+  double *xs = xb + D.vec_off[s];
+  const int *bnd = D.pool + t.bnd;
+  const int *cptr = D.pool + t.csr_ptr, *ccol = D.pool + t.csr_col;
+  const double *val = csr_val + D.csr_off[s];
+  for (int q = threadIdx.x; q < t.nbnd; q += blockDim.x) {
+    const int row = bnd[q];
+    double acc = 0.0;
+    for (int e = cptr[row]; e < cptr[row + 1]; ++e) {
+      const int c = ccol[e];
+      acc += val[e] * (ys[c] + xs[c]);
+    }
+    zsh[q] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < t.nbnd; q += blockDim.x) xs[bnd[q]] = zsh[q];
+}
+
+// ------------------------------------ coarse -----------------------------------------
+// y = G^T v : one warp per floating subdomain, lanes stride over its rows, fixed-order sum.
+__global__ void k_Gt(DevTopo D, const double *v, double *y, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (f >= D.NF) return;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int q = D.float_rows_ptr[f] + lane; q < D.float_rows_ptr[f + 1]; q += 32) {
+    const int r = D.float_rows[q];
+    const double *g = (D.lam_fa[r] == f ? D.lam_ga : D.lam_gb) + 3 * (long long)r;
+    const double vr = v[r];
+    a0 += g[0] * vr; a1 += g[1] * vr; a2 += g[2] * vr;
+  }
+  a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
+  if (lane == 0) { y[3 * f] = a0; y[3 * f + 1] = a1; y[3 * f + 2] = a2; }
+}
+
+// alpha = Hinv y : dense symmetric (G^T G)^{-1}, one warp per row
+__global__ void k_gemv(const double *Hinv, const double *y, double *alpha, int nH, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nH) return;
+  const double *h = Hinv + (long long)row * nH;
+  double acc = 0.0;
+  for (int c = lane; c < nH; c += 32) acc += h[c] * y[c];
+  acc = warp_sum(acc);
+  if (lane == 0) alpha[row] = acc;
+}
+
+// out = v + sgn * G alpha  (v may be null)
+__global__ void k_Gcomb(DevTopo D, const double *alpha, const double *v, double sgn, double *out, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= D.nlam) return;
+  double acc = 0.0;
+  const int fa = D.lam_fa[r], fb = D.lam_fb[r];
+  if (fa >= 0) acc += D.lam_ga[3 * r] * alpha[3 * fa] + D.lam_ga[3 * r + 1] * alpha[3 * fa + 1] + D.lam_ga[3 * r + 2] * alpha[3 * fa + 2];
+  if (fb >= 0) acc += D.lam_gb[3 * r] * alpha[3 * fb] + D.lam_gb[3 * r + 1] * alpha[3 * fb + 1] + D.lam_gb[3 * r + 2] * alpha[3 * fb + 2];
+  out[r] = (v ? v[r] : 0.0) + sgn * acc;
+}
+
+// ------------------------------- right-hand side --------------------------------------
+// f_s at time t: u rows the assembled loads, xi rows 0, p rows -(R eta^{n-1}) - tau Z(t)
+// (Eq. (2.42) with eta eliminated).  Writes f into xf (fixed dofs of floating subdomains
+// zeroed, the K^+ convention) and e_f = R_f^T f_f for floating subdomains.
+__global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double *Zn, const double *Reta,
+                      double t_now, double *xf, double *e) {
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const double *fs = fstat + D.vec_off[s];
+  double *x = xf + D.vec_off[s];
+  const int *dfield = D.pool + t.dof_field, *dnode = D.pool + t.dof_node;
+  const long long pn0 = D.pnode_off[s];
+  const double q_t = sin(P.q_omega * t_now);
+  const int fidx = D.sub_float[s];
+  const double hx = D.sub_hx[s], hy = D.sub_hy[s];
+  const double xc = D.sub_x0[s] + 0.5 * t.nx * hx, yc = D.sub_y0[s] + 0.5 * t.ny * hy;
+  const double L = fmax(t.nx * hx, t.ny * hy);
+  double e0 = 0, e1 = 0, e2 = 0;
+  for (int d = threadIdx.x; d < t.n; d += blockDim.x) {
+    const int f = dfield[d], node = dnode[d];
+    double v = 0.0;
+    if (f <= 1) {
+      v = fs[d];
+      if (fidx >= 0) {
+        const double xx = D.sub_x0[s] + (node % t.nux) * hx / t.k;
+        const double yy = D.sub_y0[s] + (node / t.nux) * hy / t.k;
+        if (f == 0) { e0 += v; e2 += -(yy - yc) / L * v; }
+        else { e1 += v; e2 += (xx - xc) / L * v; }
+      }
+    } else if (f == 3) {
+      double z = Zn[pn0 + node];
+      if (P.source == 1 && s == P.src_sub && node == P.src_node) z += q_t;
+      v = -Reta[pn0 + node] - P.tau * z;
+    }
+    const bool fixed = t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2);
+    x[d] = fixed ? 0.0 : v;
+  }
+  if (fidx >= 0) {
+    __shared__ double sh[32];
+    const double s0 = block_sum(e0, sh);
+    const double s1 = block_sum(e1, sh);
+    const double s2 = block_sum(e2, sh);
+    if (threadIdx.x == 0) { e[3 * fidx] = s0; e[3 * fidx + 1] = s1; e[3 * fidx + 2] = s2; }
+  }
+}
+
+// --------------------------------- recovery -------------------------------------------
+// x_s = (K^+ f)_s - (K^+ B^T lambda)_s + R_s alpha_s; canonical fields; eta; R eta.
+__global__ void k_recover(DevTopo D, DevParams P, const double *xf, const double *xl, const double *alpha,
+                          double *U, double *XI, double *ETA, double *PP, double *Reta) {
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const double *a = xf + D.vec_off[s];
+  const double *b = xl + D.vec_off[s];
+  const int *dfield = D.pool + t.dof_field, *dnode = D.pool + t.dof_node;
+  const long long un0 = D.unode_off[s], pn0 = D.pnode_off[s];
+  const int fidx = D.sub_float[s];
+  const double hx = D.sub_hx[s], hy = D.sub_hy[s];
+  const double xc = D.sub_x0[s] + 0.5 * t.nx * hx, yc = D.sub_y0[s] + 0.5 * t.ny * hy;
+  const double L = fmax(t.nx * hx, t.ny * hy);
+  for (int d = threadIdx.x; d < t.n; d += blockDim.x) {
+    const int f = dfield[d], node = dnode[d];
+    double v = a[d] - b[d];
+    if (f <= 1) {
+      if (fidx >= 0) {
+        const double xx = D.sub_x0[s] + (node % t.nux) * hx / t.k;
+        const double yy = D.sub_y0[s] + (node / t.nux) * hy / t.k;
+        const double *al = alpha + 3 * fidx;
+        if (f == 0) v += al[0] - (yy - yc) / L * al[2];
+        else v += al[1] + (xx - xc) / L * al[2];
+      }
+      U[2 * (un0 + node) + f] = v;
+    } else if (f == 2) {
+      XI[pn0 + node] = v;
+    } else {
+      PP[pn0 + node] = v;
+    }
+  }
+  __syncthreads();
+  if (!t.poro) return;
+  const double ce = P.c0 + P.alpha * P.alpha / P.lam, cx = P.alpha / P.lam;
+  const int np = t.npx * t.npy;
+  for (int node = threadIdx.x; node < np; node += blockDim.x)
+    ETA[pn0 + node] = ce * PP[pn0 + node] - cx * XI[pn0 + node];
+  __syncthreads();
+  // R eta, matrix free: every incident triangle adds area/12 (2 eta_n + eta_a + eta_b)
+  const double w = 0.5 * hx * hy / 12.0;
+  const double *E = ETA + pn0;
+  for (int node = threadIdx.x; node < np; node += blockDim.x) {
+    const int i = node % t.npx, j = node / t.npx, nx = t.nx, ny = t.ny, W = t.npx;
+    auto e = [&](int ii, int jj) { return E[jj * W + ii]; };
+    const double en = e(i, j);
+    double acc = 0.0;
+    if (i >= 1 && j >= 1) {
+      acc += 2 * en + e(i - 1, j - 1) + e(i, j - 1);
+      acc += 2 * en + e(i - 1, j - 1) + e(i - 1, j);
+    }
+    if (i < nx && j >= 1) acc += 2 * en + e(i, j - 1) + e(i + 1, j);
+    if (i >= 1 && j < ny) acc += 2 * en + e(i - 1, j) + e(i, j + 1);
+    if (i < nx && j < ny) {
+      acc += 2 * en + e(i + 1, j) + e(i + 1, j + 1);
+      acc += 2 * en + e(i + 1, j + 1) + e(i, j + 1);
+    }
+    Reta[pn0 + node] = w * acc;
+  }
+}
+
+// Dense copy of one band matrix for tests: out[r * n + c] (both triangles).
+template <typename T>
+__global__ void k_band_to_dense(const T *band, int n, int LD, int b, double *out) {
+  const long long tot = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n), c = (int)(e % n);
+    const int lo = min(r, c), hi = max(r, c);
+    out[e] = (hi - lo <= b) ? double(band[(long long)lo * LD + hi % LD]) : 0.0;
+  }
+}
+cudaError_t launch_band_to_dense(const double *band, int n, int LD, int b, double *out, cudaStream_t s) {
+  k_band_to_dense<double><<<256, 256, 0, s>>>(band, n, LD, b, out);
+  return cudaGetLastError();
+}
+
+// identity columns for the explicit coarse inverse
+__global__ void k_identity(double *X, int nH) {
+  const long long tot = (long long)nH * nH;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
+    X[e] = (e / nH == e % nH) ? 1.0 : 0.0;
+}
+
+}  // namespace fp

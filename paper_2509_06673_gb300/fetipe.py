@@ -1,0 +1,235 @@
+"""ctypes binding of libfetipe.so (argument marshalling only; every computation runs in the
+library's CUDA kernels).  Raises on import if the library has not been built: there is no
+CPU fallback.
+
+Names follow the C ABI of include/fetipe.h: ``create``, ``assemble``, ``factor``, ``step``,
+``run``, ``get_lambda``, ``get_lambda_keys``, ``get_fields``, ``apply_F``,
+``apply_precond``, ``apply_projection``, ``get_dof_map``, ``get_local_matrix``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfetipe.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libfetipe.so not built: run paper_2509_06673_gb300/build.py "
+                      "(or __graft_entry__.build()) first")
+_lib = ctypes.CDLL(LIB_PATH)
+
+FP_OK = 0
+STATUS_NAMES = {0: "FP_OK", 1: "FP_ERR_INVALID", 2: "FP_ERR_OOM", 3: "FP_ERR_CUDA",
+                4: "FP_ERR_NOT_CONVERGED", 5: "FP_ERR_BREAKDOWN", 6: "FP_ERR_TIMEOUT",
+                7: "FP_ERR_STATE"}
+FP_SOURCE_MANUFACTURED, FP_SOURCE_POINT = 0, 1
+FP_PREC_FP64, FP_PREC_MIXED = 0, 1
+FP_PRECOND_DIRICHLET, FP_PRECOND_NONE = 0, 2
+
+EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_get_sizes",
+            "fp_get_lambda", "fp_get_lambda_keys", "fp_get_fields", "fp_apply_F",
+            "fp_apply_precond", "fp_apply_projection", "fp_get_dof_map",
+            "fp_get_local_matrix", "fp_get_step_timing", "fp_last_error", "fp_destroy"]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nsub_x", ctypes.c_int), ("nsub_y", ctypes.c_int),
+                ("cells_x", ctypes.POINTER(ctypes.c_int)), ("cells_y", ctypes.POINTER(ctypes.c_int)),
+                ("poro_rows", ctypes.c_int), ("order_k", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lame_lambda", ctypes.c_double), ("mu", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("c0", ctypes.c_double),
+                ("perm_k", ctypes.c_double), ("mu_f", ctypes.c_double), ("tau", ctypes.c_double),
+                ("perm", ctypes.POINTER(ctypes.c_double)), ("source", ctypes.c_int),
+                ("src_i", ctypes.c_int), ("src_j", ctypes.c_int), ("q_omega", ctypes.c_double),
+                ("precision", ctypes.c_int), ("precond", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_it", ctypes.c_int)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("nsub", ctypes.c_int), ("n_floating", ctypes.c_int), ("n_lambda", ctypes.c_int),
+                ("n_lambda_p", ctypes.c_int), ("n_dofs", ctypes.c_longlong),
+                ("n_unode_total", ctypes.c_longlong), ("n_pnode_total", ctypes.c_longlong),
+                ("factor_bytes", ctypes.c_longlong), ("max_half_band", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_lib.fp_create.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), _vp, ctypes.POINTER(_vp)]
+for _n in ("fp_assemble", "fp_factor"):
+    getattr(_lib, _n).argtypes = [_vp]
+_lib.fp_step.argtypes = [_vp, ctypes.POINTER(StepStats)]
+_lib.fp_run.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(StepStats)]
+_lib.fp_get_sizes.argtypes = [_vp, ctypes.POINTER(Sizes)]
+_lib.fp_get_lambda.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.fp_get_lambda_keys.argtypes = [_vp, _vp]
+_lib.fp_get_fields.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+for _n in ("fp_apply_F", "fp_apply_precond", "fp_apply_projection"):
+    getattr(_lib, _n).argtypes = [_vp, _vp, _vp, ctypes.c_int]
+_lib.fp_get_dof_map.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int)]
+_lib.fp_get_local_matrix.argtypes = [_vp, ctypes.c_int, _vp]
+_lib.fp_get_step_timing.argtypes = [_vp, _vp]
+_lib.fp_last_error.argtypes = [_vp]
+_lib.fp_last_error.restype = ctypes.c_char_p
+_lib.fp_destroy.argtypes = [_vp]
+
+
+class FetipeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(a):
+    """Host numpy array or torch tensor -> (pointer, on_device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+class Solver:
+    """One fetipe handle.  ``case`` is a workloads.Case."""
+
+    def __init__(self, case, stream=None, precision=None):
+        self._h = _vp()
+        cx = np.ascontiguousarray(case.cells_x, dtype=np.int32)
+        cy = np.ascontiguousarray(case.cells_y, dtype=np.int32)
+        self._keep = [cx, cy]
+        mesh = MeshDesc(case.nsub_x, case.nsub_y, cx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        cy.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), case.poro_rows, case.order_k)
+        perm_ptr = None
+        if case.perm is not None:
+            perm = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in case.perm]))
+            self._keep.append(perm)
+            perm_ptr = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        src = {"manufactured": FP_SOURCE_MANUFACTURED, "point": FP_SOURCE_POINT}[case.source]
+        prec = precision or case.precision
+        par = Params(case.lame_lambda, case.mu, case.alpha, case.c0, case.perm_k, case.mu_f, case.tau,
+                     perm_ptr, src, int(case.src_node[0]), int(case.src_node[1]), float(case.q_omega),
+                     FP_PREC_MIXED if prec == "mixed" else FP_PREC_FP64,
+                     FP_PRECOND_NONE if case.precond == "none" else FP_PRECOND_DIRICHLET,
+                     case.tol, case.max_it)
+        st = _lib.fp_create(ctypes.byref(mesh), ctypes.byref(par), stream, ctypes.byref(self._h))
+        if st != FP_OK:
+            raise FetipeError(st, _lib.fp_last_error(None).decode())
+        self.case = case
+        s = Sizes()
+        self._check(_lib.fp_get_sizes(self._h, ctypes.byref(s)))
+        self.sizes = s
+
+    def _check(self, st):
+        if st != FP_OK:
+            raise FetipeError(st, _lib.fp_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            _lib.fp_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # pipeline -------------------------------------------------------------------
+    def assemble(self):
+        self._check(_lib.fp_assemble(self._h))
+
+    def factor(self):
+        self._check(_lib.fp_factor(self._h))
+
+    def step(self, allow_failure=False):
+        st = StepStats()
+        rc = _lib.fp_step(self._h, ctypes.byref(st))
+        if not allow_failure:
+            self._check(rc)
+        return {"status": rc, "step": st.step, "iterations": st.iterations,
+                "rel_residual": st.rel_residual, "true_rel_residual": st.true_rel_residual}
+
+    def run(self, n_steps):
+        st = StepStats()
+        self._check(_lib.fp_run(self._h, n_steps, ctypes.byref(st)))
+        return {"step": st.step, "iterations": st.iterations, "rel_residual": st.rel_residual,
+                "true_rel_residual": st.true_rel_residual}
+
+    # outputs --------------------------------------------------------------------
+    def get_lambda(self, out=None):
+        out = np.empty(self.sizes.n_lambda) if out is None else out
+        p, dev = _ptr(out)
+        self._check(_lib.fp_get_lambda(self._h, p, dev))
+        return out
+
+    def get_lambda_keys(self):
+        k = np.empty((self.sizes.n_lambda, 6), dtype=np.int32)
+        self._check(_lib.fp_get_lambda_keys(self._h, k.ctypes.data))
+        return k
+
+    def get_fields(self):
+        s = self.sizes
+        u = np.empty(2 * s.n_unode_total)
+        xi = np.empty(s.n_pnode_total)
+        eta = np.empty(s.n_pnode_total)
+        p = np.empty(s.n_pnode_total)
+        self._check(_lib.fp_get_fields(self._h, u.ctypes.data, xi.ctypes.data, eta.ctypes.data,
+                                       p.ctypes.data, 0))
+        return u, xi, eta, p
+
+    def _op(self, fn, v):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.empty_like(v)
+        self._check(fn(self._h, v.ctypes.data, out.ctypes.data, 0))
+        return out
+
+    def apply_F(self, v):
+        return self._op(_lib.fp_apply_F, v)
+
+    def apply_precond(self, v):
+        return self._op(_lib.fp_apply_precond, v)
+
+    def apply_projection(self, v):
+        return self._op(_lib.fp_apply_projection, v)
+
+    def get_dof_map(self, s):
+        n = ctypes.c_int()
+        self._check(_lib.fp_get_dof_map(self._h, s, None, None, ctypes.byref(n)))
+        f = np.empty(n.value, dtype=np.int32)
+        nd = np.empty(n.value, dtype=np.int32)
+        self._check(_lib.fp_get_dof_map(self._h, s, f.ctypes.data, nd.ctypes.data, ctypes.byref(n)))
+        return f, nd
+
+    def get_local_matrix(self, s):
+        f, _ = self.get_dof_map(s)
+        A = np.empty((f.size, f.size))
+        self._check(_lib.fp_get_local_matrix(self._h, s, A.ctypes.data))
+        return A
+
+    def step_timing(self):
+        t = np.zeros(4)
+        self._check(_lib.fp_get_step_timing(self._h, t.ctypes.data))
+        return t
+
+
+def split_fields(case, u, xi, eta, p):
+    """Per-subdomain views of the canonical field arrays (same layout as the C ABI)."""
+    out = []
+    ou = op = 0
+    k = case.order_k
+    for s in range(case.nsub):
+        nx = case.cells_x[s % case.nsub_x]
+        ny = case.cells_y[s // case.nsub_x]
+        nun = (k * nx + 1) * (k * ny + 1)
+        npn = (nx + 1) * (ny + 1)
+        out.append((u[2 * ou: 2 * (ou + nun)].reshape(-1, 2), xi[op: op + npn], eta[op: op + npn],
+                    p[op: op + npn]))
+        ou += nun
+        op += npn
+    return out
