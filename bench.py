@@ -1,0 +1,277 @@
+#!/usr/bin/env python
+"""Benchmark of the FETI interface solve: backward-Euler time steps per second.
+
+One step = the whole per-step hot path: right-hand side, d = B K^+ f, lambda_0, the PCG
+loop of Algorithm 1 (F p, coarse projection, Dirichlet preconditioner, reductions) to a
+relative projected residual of `tol`, and the recovery of (u, xi, eta, p).
+
+Arms
+  native (default)   the CUDA library, one independent replica per GPU ("replicas only":
+                     the solve of one problem does not shard across GPUs in this build).
+  --impl reference   the CPU oracle (plain FP64 scipy FETI) on the host cores, on a bounded
+                     sample of the same workload (a smaller partition of the same
+                     subdomains), scaled to the full workload by the subdomain count.
+
+Output: one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time steps/s at lambda rel. residual 1e-8"
+
+
+def workload(name, precision=None):
+    from paper_2509_06673_gb300 import workloads as W
+    cfg = {"config2": W.config2, "config3": W.config3, "config5": W.config5}[name]()
+    cfg = cfg.with_(tol=1e-8, max_it=2000)
+    if precision:
+        cfg = cfg.with_(precision=precision)
+    return cfg
+
+
+def sample_of(case):
+    """Bounded CPU sample: a 4 x 4 partition of subdomains of the same size and physics."""
+    from paper_2509_06673_gb300 import workloads as W
+    cx = case.cells_x[:4]
+    cy = case.cells_y[:4]
+    s = W.grid_case("sample", 4, 4, list(cx), list(cy), order_k=case.order_k,
+                    lame_lambda=case.lame_lambda, mu=case.mu, alpha=case.alpha, c0=case.c0,
+                    perm_k=case.perm_k, mu_f=case.mu_f, tau=case.tau, tol=case.tol, max_it=case.max_it)
+    if case.perm is not None:
+        s = s.with_(perm=[case.perm[(r * case.nsub_x) + c] for r in range(4) for c in range(4)])
+    return s
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [l.split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm = sorted(float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit())
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate of the profiling recipe's table
+
+
+def cpu_baseline(case, n_steps=1):
+    """Oracle FETI on the bounded sample; returns (steps/s scaled to the full workload, info)."""
+    from oracle.monolithic import Discretization
+    from oracle.feti import FETI
+    smp = sample_of(case)
+    d = Discretization(smp)
+    f = FETI(smp, d)
+    t0 = time.perf_counter()
+    st = f.run(n_steps=n_steps)
+    dt = (time.perf_counter() - t0) / n_steps
+    scale = smp.nsub / case.nsub
+    return 1.0 / dt * scale, {
+        "sample": "%d step(s) of a 4x4 partition of the same subdomains (%dx%d cells, same physics), "
+                  "oracle setup excluded; steps/s scaled by %d/%d subdomains; %d PCG iterations"
+                  % (n_steps, smp.cells_x[0], smp.cells_y[0], smp.nsub, case.nsub, st[-1]["iterations"]),
+        "cores": 1,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    case = workload(args.config, args.precision)
+    from oracle.monolithic import Discretization
+    from oracle.feti import FETI
+    smp = sample_of(case)
+    d = Discretization(smp)
+    f = FETI(smp, d)
+    f.run(n_steps=args.warmup)
+    t0 = time.perf_counter()
+    f.run(n_steps=args.steps)
+    dt = time.perf_counter() - t0
+    scale = smp.nsub / case.nsub
+    value = args.steps / dt * scale
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": case.name, "tol": case.tol},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "steps/s",
+                             "sample": "4x4 partition of the same subdomains, %d steps after %d warm-up, "
+                                       "scaled by %d/%d subdomains" % (args.steps, args.warmup, smp.nsub, case.nsub)},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2509_06673_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2509_06673_gb300 import fetipe as F
+    case = workload(args.config, args.precision)
+    stream = torch.cuda.current_stream()
+    sol = F.Solver(case, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    sol.assemble()
+    sol.factor()
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        sol.step()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM ----------------------------------
+    sol.set_profiling(True)
+    clocks = Clocks(local)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    its = []
+    for _ in range(args.steps):
+        its.append(sol.step()["iterations"])
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kN, kD = sol.kernel_stats(0), sol.kernel_stats(1)
+    sol.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+    # ---- end to end through the public API, host buffers ------------------------------
+    s = sol.sizes
+    lam_h = torch.empty(s.n_lambda, dtype=torch.float64).pin_memory().numpy()
+    u_h = torch.empty(2 * s.n_unode_total, dtype=torch.float64).pin_memory().numpy()
+    f_h = [torch.empty(s.n_pnode_total, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sol.step()
+        sol.get_lambda(lam_h)
+        F._lib.fp_get_fields(sol._h, u_h.ctypes.data, f_h[0].ctypes.data, f_h[1].ctypes.data,
+                             f_h[2].ctypes.data, 0)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    d2h = 8 * (s.n_lambda + 2 * s.n_unode_total + 3 * s.n_pnode_total)
+    # ---- roofline of the dominant kernel (banded local solves) -------------------------
+    launches = kN["launches"] + kD["launches"]
+    avg_ms = (kN["total_ms"] + kD["total_ms"]) / max(launches, 1)
+    hbm, src = peaks()
+    if case.precision == "fp64":
+        ach = kN["flops_per_launch"] / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_band_solve<double>", "peak_source": "nominal FP64 rate (derived)",
+                "achieved_gbs": kN["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9}
+    else:
+        ach = kN["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": "k_band_solve<float>", "peak_source": src + " (burst copy)"}
+    roof.update({"launches": launches, "avg_launch_ms": avg_ms,
+                 "share_of_step": (kN["total_ms"] + kD["total_ms"]) / ms})
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if case.precision == "fp64" else "f32 local / f64 outer",
+            "data": "synthetic",
+            "config": {"workload": case.name, "precision": case.precision, "tol": case.tol,
+                       "subdomains": case.nsub, "n_lambda": s.n_lambda, "dofs": s.n_dofs,
+                       "factor_gb": s.factor_bytes / 1e9, "l2": "inputs larger than L2 (factors %.1f GB)"
+                       % (s.factor_bytes / 1e9), "setup_s": setup_s, "pcg_iterations": its,
+                       "parallelism": "replicas (one independent problem per GPU)"},
+            "roofline": roof, "clocks": clk,
+            "e2e": {"value": world * args.steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": None}
+    # kernel launches of the library in the timed region (counted from the loop structure)
+    line["gpu_launches"] = int(launches + sum(its) * 22 + args.steps * 40)
+    if rank == 0 and not args.no_cpu_baseline:
+        v, info = cpu_baseline(case)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": info["cores"], "kind": "oracle",
+                                "sample": info["sample"]}
+    sol.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--config", default="config2", choices=["config2", "config3", "config5"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
