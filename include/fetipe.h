@@ -172,6 +172,19 @@ fp_status fp_apply_F(fp_handle *h, const double *v, double *out, int on_device);
 fp_status fp_apply_precond(fp_handle *h, const double *v, double *out, int on_device);
 fp_status fp_apply_projection(fp_handle *h, const double *v, double *out, int on_device);
 
+/* Same result as fp_apply_projection, for callers that cannot allocate device memory at
+ * call time (for instance while a CUDA stream is being captured into a graph, or inside a
+ * runtime that owns every allocation).  The paper has no counterpart: this is a library
+ * convenience.  v and out are device pointers of the handle's device (n_lambda doubles;
+ * they may alias).  The call allocates nothing: its scratch (two vectors of 3 * n_floating
+ * doubles) is a fixed array of 2 * 24576 doubles (384 KiB) compiled into the library and
+ * kept on every device that loads it until the process exits; more than 8192 floating
+ * subdomains is rejected with FP_ERR_INVALID.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress), so make it before any stream capture.
+ * Every call shares the array: calls that overlap on the GPU (other streams, other
+ * threads, other handles on the same device) race; serialise them.  Synchronous. */
+fp_status fp_apply_projection_noalloc(fp_handle *h, const double *v, double *out);
+
 /* Local dof map of subdomain s (host, n_s ints each): field (0 u_x, 1 u_y, 2 xi, 3 p) and
  * node index on the subdomain's grid (displacement grid for u, P1 grid otherwise). */
 fp_status fp_get_dof_map(const fp_handle *h, int s, int *field, int *node, int *n_out);
@@ -183,6 +196,21 @@ fp_status fp_get_local_matrix(const fp_handle *h, int s, double *dense);
 /* Device time of the last fp_step split by phase (milliseconds, CUDA events):
  * [0] rhs + d, [1] PCG loop, [2] recovery; [3] total local-solve time of the step. */
 fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
+
+/* Per-kernel-class timing (CUDA events on the handle's stream around every launch of the
+ * class; off by default).  kind 0: Neumann local solves (K_s^+), 1: Dirichlet local solves
+ * (the preconditioner).  bytes_per_launch / flops_per_launch are algorithmic figures: every
+ * band entry read once per sweep (2 sweeps, entry size of the factor precision) plus the
+ * right-hand side / solution traffic (4 doubles per row), and 2 flops per band entry per
+ * sweep.  fp_set_profiling(h, 1) also resets the counters. */
+typedef struct {
+  long long launches;
+  double total_ms;
+  double bytes_per_launch;
+  double flops_per_launch;
+} fp_kernel_stats;
+fp_status fp_set_profiling(fp_handle *h, int on);
+fp_status fp_get_kernel_stats(const fp_handle *h, int kind, fp_kernel_stats *out);
 
 const char *fp_last_error(const fp_handle *h);
 void fp_destroy(fp_handle *h);

@@ -2,6 +2,7 @@
 // backward-Euler step (Sec. 2.5) solved by FETI (Sec. 3, Algorithm 1).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -78,6 +79,14 @@ struct fp_handle {
   cudaEvent_t ev[6] = {};
   double last_ms[4] = {0, 0, 0, 0};
   int nbnd_max = 0;
+  // profiling of the local-solve launches
+  int profiling = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> pending;  // (kind, index of the start event)
+  long long prof_launches[2] = {0, 0};
+  double prof_ms[2] = {0, 0};
+  double bytes_per_solve = 0, flops_per_solve = 0;
 };
 
 namespace {
@@ -273,10 +282,45 @@ fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask
   return FP_OK;
 }
 
+fp_status next_event(fp_handle *h, cudaEvent_t *e) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t ne;
+    CK(cudaEventCreate(&ne));
+    h->ev_pool.push_back(ne);
+  }
+  *e = h->ev_pool[h->ev_used++];
+  return FP_OK;
+}
+
 fp_status solve_local(fp_handle *h, bool dirichlet, double *x, const int *done) {
   const void *fac = dirichlet ? h->facD : h->facN;
   const BandTask *tasks = dirichlet ? h->tasksD : h->tasksN;
-  return launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, x, h->mmax, done);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->profiling) {
+    h->pending.push_back({dirichlet ? 1 : 0, h->ev_used});
+    TRY(next_event(h, &e0));
+    TRY(next_event(h, &e1));
+    CK(cudaEventRecord(e0, h->stream));
+  }
+  TRY(launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, x, h->mmax, done));
+  if (h->profiling) CK(cudaEventRecord(e1, h->stream));
+  return FP_OK;
+}
+
+// After a stream synchronisation: fold the pending event pairs into the counters.  A
+// launch that returned at once because the PCG had already converged is not counted.
+fp_status collect_profile(fp_handle *h) {
+  for (auto &pr : h->pending) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]));
+    if (ms > 0.002f) {
+      h->prof_launches[pr.first] += 1;
+      h->prof_ms[pr.first] += ms;
+    }
+  }
+  h->pending.clear();
+  h->ev_used = 0;
+  return FP_OK;
 }
 
 fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
@@ -426,6 +470,14 @@ fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cud
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   fp_status st = build_device(h);
   if (st != FP_OK) { g_create_err = h->err; fp_destroy(h); return st; }
+  {
+    const double esz = h->P.precision == FP_PREC_MIXED ? 4.0 : 8.0;
+    for (int s = 0; s < h->T.S; ++s) {
+      const Template &t = h->T.tpl[h->T.sub_tpl[s]];
+      h->bytes_per_solve += 2.0 * t.n * (t.b + 1) * esz + 4.0 * t.n * 8.0;
+      h->flops_per_solve += 4.0 * t.n * t.b + t.n;
+    }
+  }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) { fp_destroy(h); return FP_ERR_CUDA; }
   *out = h;
   return FP_OK;
@@ -552,6 +604,7 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  TRY(collect_profile(h));
   float ms01 = 0, ms12 = 0, ms23 = 0;
   cudaEventElapsedTime(&ms01, h->ev[0], h->ev[1]);
   cudaEventElapsedTime(&ms12, h->ev[1], h->ev[2]);
@@ -637,6 +690,7 @@ static fp_status apply_op_abi(fp_handle *h, const double *v, double *out, int on
                               : apply_P(h, vin, h->q, h->fl_zero);
   if (st) return st;
   TRY(copy_out(h, out, h->q, bytes, on_device));
+  TRY(collect_profile(h));
   return check_status(h);
 }
 
@@ -685,6 +739,25 @@ fp_status fp_get_step_timing(const fp_handle *h, double *ms4) {
   return FP_OK;
 }
 
+fp_status fp_set_profiling(fp_handle *h, int on) {
+  if (!h) return FP_ERR_INVALID;
+  h->profiling = on ? 1 : 0;
+  h->prof_launches[0] = h->prof_launches[1] = 0;
+  h->prof_ms[0] = h->prof_ms[1] = 0;
+  h->pending.clear();
+  h->ev_used = 0;
+  return FP_OK;
+}
+
+fp_status fp_get_kernel_stats(const fp_handle *h, int kind, fp_kernel_stats *out) {
+  if (!h || !out || kind < 0 || kind > 1) return FP_ERR_INVALID;
+  out->launches = h->prof_launches[kind];
+  out->total_ms = h->prof_ms[kind];
+  out->bytes_per_launch = h->bytes_per_solve;
+  out->flops_per_launch = h->flops_per_solve;
+  return FP_OK;
+}
+
 const char *fp_last_error(const fp_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
 void fp_destroy(fp_handle *h) {
@@ -694,7 +767,73 @@ void fp_destroy(fp_handle *h) {
   if (h->h_sc) cudaFreeHost(h->h_sc);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : h->ev_pool) cudaEventDestroy(e);
   delete h;
 }
 
 }  // extern "C"
+
+// =========================== projection without allocation ==========================
+// fp_apply_projection_noalloc: the coarse projection of fp_apply_projection for callers
+// that may not allocate device memory at call time -- for instance code that runs while a
+// CUDA stream is being captured into a graph, or an embedding runtime that owns every
+// allocation itself.  Its two scratch vectors (G^T v and (G^T G)^{-1} G^T v) live in the
+// file-scope array below instead of handle memory, so the call performs no cudaMalloc,
+// cudaFree or allocating library call.  The array is fixed at compile time:
+// kNoAllocMaxCoarse coarse unknowns (3 per floating subdomain, i.e. up to 8192 floating
+// subdomains), 2 * 24576 doubles = 384 KiB on every device that loads this library, held
+// until the process exits.  Host code cannot use the array's name as a device address; the
+// address is obtained with cudaGetSymbolAddress once per device, with that device current,
+// during the first call on the device.
+namespace {
+constexpr int kNoAllocMaxCoarse = 3 * 8192;
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxCoarse];
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[128] = {nullptr};
+}  // namespace
+
+extern "C" fp_status fp_apply_projection_noalloc(fp_handle *h, const double *v, double *out) {
+  if (!h || !v || !out) return FP_ERR_INVALID;
+  if (h->stage < 2) { h->err = "fp_apply_projection_noalloc before fp_factor"; return FP_ERR_STATE; }
+  const Topology &T = h->T;
+  if (T.nH > kNoAllocMaxCoarse) {
+    h->err = "fp_apply_projection_noalloc: " + std::to_string(T.nH) + " coarse unknowns exceed the fixed scratch of " +
+             std::to_string(kNoAllocMaxCoarse) + " (8192 floating subdomains); use fp_apply_projection";
+    return FP_ERR_INVALID;
+  }
+  int prev = -1;
+  CK(cudaGetDevice(&prev));
+  if (prev != h->device) CK(cudaSetDevice(h->device));
+  fp_status st = FP_OK;
+  do {
+    if (!T.NF) {
+      if (out != v) {
+        cudaError_t e = cudaMemcpyAsync(out, v, T.n_lambda * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = FP_ERR_CUDA; break; }
+      }
+    } else {
+      double *scratch = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (h->device < 0 || h->device >= 128) { h->err = "device index out of range"; st = FP_ERR_INVALID; break; }
+        if (!g_noalloc_addr[h->device]) {
+          void *p = nullptr;
+          cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+          if (e != cudaSuccess) { h->err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e); st = FP_ERR_CUDA; break; }
+          g_noalloc_addr[h->device] = static_cast<double *>(p);
+        }
+        scratch = g_noalloc_addr[h->device];
+      }
+      double *cy = scratch, *ca = scratch + kNoAllocMaxCoarse;
+      k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, cy, h->fl_zero);
+      k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, h->stream>>>(h->Hinv, cy, ca, T.nH, h->fl_zero);
+      k_Gcomb<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, ca, v, -1.0, out, h->fl_zero);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { h->err = std::string("kernel launch: ") + cudaGetErrorString(e); st = FP_ERR_CUDA; break; }
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = FP_ERR_CUDA; }
+  } while (0);
+  if (prev != h->device) cudaSetDevice(prev);
+  return st;
+}

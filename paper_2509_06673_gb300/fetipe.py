@@ -28,8 +28,10 @@ FP_PRECOND_DIRICHLET, FP_PRECOND_NONE = 0, 2
 
 EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_get_sizes",
             "fp_get_lambda", "fp_get_lambda_keys", "fp_get_fields", "fp_apply_F",
-            "fp_apply_precond", "fp_apply_projection", "fp_get_dof_map",
-            "fp_get_local_matrix", "fp_get_step_timing", "fp_last_error", "fp_destroy"]
+            "fp_apply_precond", "fp_apply_projection", "fp_apply_projection_noalloc",
+            "fp_get_dof_map",
+            "fp_get_local_matrix", "fp_get_step_timing", "fp_set_profiling",
+            "fp_get_kernel_stats", "fp_last_error", "fp_destroy"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -55,6 +57,11 @@ class Sizes(ctypes.Structure):
                 ("factor_bytes", ctypes.c_longlong), ("max_half_band", ctypes.c_int)]
 
 
+class KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double),
+                ("bytes_per_launch", ctypes.c_double), ("flops_per_launch", ctypes.c_double)]
+
+
 class StepStats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("iterations", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double)]
@@ -72,9 +79,12 @@ _lib.fp_get_lambda_keys.argtypes = [_vp, _vp]
 _lib.fp_get_fields.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
 for _n in ("fp_apply_F", "fp_apply_precond", "fp_apply_projection"):
     getattr(_lib, _n).argtypes = [_vp, _vp, _vp, ctypes.c_int]
+_lib.fp_apply_projection_noalloc.argtypes = [_vp, _vp, _vp]
 _lib.fp_get_dof_map.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int)]
 _lib.fp_get_local_matrix.argtypes = [_vp, ctypes.c_int, _vp]
 _lib.fp_get_step_timing.argtypes = [_vp, _vp]
+_lib.fp_set_profiling.argtypes = [_vp, ctypes.c_int]
+_lib.fp_get_kernel_stats.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(KernelStats)]
 _lib.fp_last_error.argtypes = [_vp]
 _lib.fp_last_error.restype = ctypes.c_char_p
 _lib.fp_destroy.argtypes = [_vp]
@@ -198,6 +208,11 @@ class Solver:
     def apply_projection(self, v):
         return self._op(_lib.fp_apply_projection, v)
 
+    def apply_projection_noalloc(self, v, out):
+        """v, out: CUDA tensors (float64, n_lambda) on the handle's device."""
+        self._check(_lib.fp_apply_projection_noalloc(self._h, v.data_ptr(), out.data_ptr()))
+        return out
+
     def get_dof_map(self, s):
         n = ctypes.c_int()
         self._check(_lib.fp_get_dof_map(self._h, s, None, None, ctypes.byref(n)))
@@ -211,6 +226,15 @@ class Solver:
         A = np.empty((f.size, f.size))
         self._check(_lib.fp_get_local_matrix(self._h, s, A.ctypes.data))
         return A
+
+    def set_profiling(self, on=True):
+        self._check(_lib.fp_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self, kind):
+        s = KernelStats()
+        self._check(_lib.fp_get_kernel_stats(self._h, kind, ctypes.byref(s)))
+        return {"launches": s.launches, "total_ms": s.total_ms,
+                "bytes_per_launch": s.bytes_per_launch, "flops_per_launch": s.flops_per_launch}
 
     def step_timing(self):
         t = np.zeros(4)
