@@ -44,7 +44,7 @@ typedef enum {
   FP_ERR_STATE = 7           /* call out of order (e.g. fp_step before fp_factor) */
 } fp_status;
 
-enum { FP_SOURCE_MANUFACTURED = 0, FP_SOURCE_POINT = 1 };
+enum { FP_SOURCE_MANUFACTURED = 0, FP_SOURCE_POINT = 1, FP_SOURCE_MANUFACTURED_T = 2 };
 enum { FP_PREC_FP64 = 0, FP_PREC_MIXED = 1 };
 enum { FP_PRECOND_DIRICHLET = 0, FP_PRECOND_NONE = 2 };
 
@@ -74,6 +74,8 @@ typedef struct {
  *        id order, elements in the order above (host pointer, copied).
  *  source: FP_SOURCE_MANUFACTURED -- the closed-form solution of Test Case 1 (Sec. 4.1)
  *            with its sources; eta^0 is the L2 projection of c0 p + alpha div u.
+ *          FP_SOURCE_MANUFACTURED_T -- the same closed form times g(t) = 1 + t (every
+ *            source times g(t); z gains g'(t) eta_0); backward Euler is exact in time for it.
  *          FP_SOURCE_POINT -- f = 0 and a point fluid source z = sin(q_omega t) at the P1
  *            vertex with global P1 grid indices (src_i, src_j) (must lie strictly inside
  *            one poroelastic subdomain); zero initial data.
@@ -196,6 +198,16 @@ fp_status fp_get_local_matrix(const fp_handle *h, int s, double *dense);
 /* Device time of the last fp_step split by phase (milliseconds, CUDA events):
  * [0] rhs + d, [1] PCG loop, [2] recovery; [3] total local-solve time of the step. */
 fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
+
+/* Tunables of the solve (defaults in brackets); FP_ERR_INVALID for an unknown key or a value
+ * out of range.
+ *   "ir_sweeps"    [6]  maximum FP64 refinement sweeps of the accurate local solves (mixed
+ *                       precision: d = B K^+ f, the true residual, the recovery), 0..16
+ *   "ir_eps"       [1e-13] refinement stops once ||dx||_2 <= ir_eps ||x||_2 (all subdomains)
+ *   "inner_ir"     [0]  refinement sweeps of the local solves inside the PCG loop, 0..8
+ *   "max_restarts" [8]  restarts of PCG from the true residual, 0..64
+ *   "pcg_chunk"    [8]  PCG iterations launched between two host polls of the stop flag, 1..256 */
+fp_status fp_set_option(fp_handle *h, const char *key, double value);
 
 /* Per-kernel-class timing (CUDA events on the handle's stream around every launch of the
  * class; off by default).  kind 0: Neumann local solves (K_s^+), 1: Dirichlet local solves

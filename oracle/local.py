@@ -21,7 +21,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import fem
-from .problem import Manufactured, kappas, barry_mercer_p2
+from .problem import Manufactured, kappas, barry_mercer_p2, time_factor
 
 
 def _dirichlet(case, m):
@@ -124,7 +124,7 @@ class LocalSystem:
         self.F_full = np.zeros(nU)
         self.Z_full = np.zeros(nP)
         self.eta0_load = np.zeros(nP)
-        if case.source == "manufactured":
+        if case.source in ("manufactured", "manufactured_t"):
             mf = Manufactured(case.lame_lambda, case.mu, case.alpha, case.c0, case.perm_k, case.mu_f)
             f = mf.f_P if m.is_poro else mf.f_E
             np.add.at(self.F_full, udofs, fem.load_vector_u(m.elem_xy, m.k, f))
@@ -159,9 +159,10 @@ class LocalSystem:
         """Right-hand side at time t given R eta^{n-1} (full P1 vector)."""
         case = self.case
         b = np.zeros(self.n)
-        b[: self.nu] = self.F_full[self.ufree]
+        g, dg = time_factor(t) if case.source == "manufactured_t" else (1.0, 0.0)
+        b[: self.nu] = g * self.F_full[self.ufree]
         if self.m.is_poro:
-            Z = self.Z_full.copy()
+            Z = g * self.Z_full + dg * self.eta0_load
             pn = self.point_node()
             if pn >= 0:
                 Z[pn] += np.sin(case.q_omega * t)

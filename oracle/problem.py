@@ -10,6 +10,10 @@
   pinned by tests/test_oracle_problem.py against central finite differences of the
   closed forms, and against the transmission conditions (2.12)-(2.14).
 * Barry-Mercer-type data of Sec. 4.3 and the point fluid source z = q(t) delta(x - x_s).
+* Time-dependent variant ``manufactured_t``: the same closed form times g(t) = 1 + t.
+  Backward Euler is exact in time for it (the time derivative is constant), and every
+  source is the stationary one times g(t), except z, which gains g'(t) eta:
+  z(t) = g(t) z_s + g'(t) (c0 p_s + alpha div u_s).
 """
 import numpy as np
 
@@ -118,6 +122,11 @@ class Manufactured:
         a = 2 * PI * self.mu * np.sin(2 * PI * x)
         b = 2 * PI * (self.lam + 2 * self.mu) * np.sin(2 * PI * x) + self.alpha * np.sin(PI * x)
         return a, b
+
+
+def time_factor(t):
+    """g(t) = 1 + t and g'(t) = 1 of the time-dependent manufactured variant."""
+    return 1.0 + t, 1.0
 
 
 def barry_mercer_p2(x, t):

@@ -35,12 +35,15 @@ __global__ void k_bnd_apply(DevTopo, const double *, const double *, double *, c
 __global__ void k_Gt(DevTopo, const double *, double *, const int *);
 __global__ void k_gemv(const double *, const double *, double *, int, const int *);
 __global__ void k_Gcomb(DevTopo, const double *, const double *, double, double *, const int *);
-__global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, double, double *,
-                      double *);
+__global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, const double *, double,
+                      double *, double *);
 __global__ void k_recover(DevTopo, DevParams, const double *, const double *, const double *, double *, double *,
                           double *, double *, double *);
 cudaError_t launch_band_to_dense(const double *band, int n, int LD, int b, double *out, cudaStream_t s);
 __global__ void k_identity(double *, int);
+__global__ void k_residual_N(DevTopo, const double *, const double *, const double *, double *, const int *);
+__global__ void k_local_add(double *, const double *, long long, const int *);
+__global__ void k_ir_check(const double *, const double *, long long, double, double *, unsigned *, int *);
 
 }  // namespace fp
 
@@ -68,12 +71,20 @@ struct fp_handle {
   int *counter = nullptr, *status = nullptr;
   // vectors
   double *X2 = nullptr, *XB = nullptr, *XP = nullptr, *XY = nullptr;
+  double *XF = nullptr, *XA = nullptr, *XR = nullptr;  // rhs, refined solution, residual
+  // tunables (fp_set_option)
+  int ir_sweeps = 6;       // max refinement sweeps of the accurate local solves (mixed precision)
+  double ir_eps = 1e-13;   // refinement stops once ||dx|| <= ir_eps ||x||
+  int inner_ir = 0;        // refinement sweeps inside the PCG loop (mixed precision)
+  int max_restarts = 8;    // PCG restarts from the true residual
+  int pcg_chunk = 8;       // PCG iterations launched between host polls
+  int restarts_last = 0;
   double *lam = nullptr, *lam_prev = nullptr, *lam00 = nullptr, *d = nullptr, *r = nullptr, *z = nullptr,
          *p = nullptr, *q = nullptr, *t1 = nullptr, *t2 = nullptr;
   double *ce = nullptr, *cy = nullptr, *calpha = nullptr;
   double *partial = nullptr, *sc = nullptr;
   unsigned *red_counter = nullptr;
-  int *fl = nullptr, *fl_zero = nullptr, *h_fl = nullptr;
+  int *fl = nullptr, *fl_zero = nullptr, *fl_ir = nullptr, *h_fl = nullptr;
   double *h_sc = nullptr;
   double *U = nullptr, *XI = nullptr, *ETA = nullptr, *PP = nullptr;
   cudaEvent_t ev[6] = {};
@@ -247,15 +258,18 @@ fp_status build_device(fp_handle *h) {
   TRY(dalloc(h, &h->E0n, (size_t)T.pnode_off[T.S]));
   TRY(dalloc(h, &h->Reta, (size_t)T.pnode_off[T.S]));
   for (double **v : {&h->X2, &h->XB, &h->XP, &h->XY}) TRY(dalloc(h, v, (size_t)nv));
+  if (h->P.precision == FP_PREC_MIXED)
+    for (double **v : {&h->XF, &h->XA, &h->XR}) TRY(dalloc(h, v, (size_t)nv));
   for (double **v : {&h->lam, &h->lam_prev, &h->lam00, &h->d, &h->r, &h->z, &h->p, &h->q, &h->t1, &h->t2})
     TRY(dalloc(h, v, (size_t)nl));
   const size_t nc = std::max(T.nH, 1);
   for (double **v : {&h->ce, &h->cy, &h->calpha}) TRY(dalloc(h, v, nc));
-  TRY(dalloc(h, &h->partial, RED_BLOCKS));
+  TRY(dalloc(h, &h->partial, 2 * RED_BLOCKS));
   TRY(dalloc(h, &h->sc, SC_N));
   TRY(dalloc(h, &h->red_counter, 4));
   TRY(dalloc(h, &h->fl, FL_N));
   TRY(dalloc(h, &h->fl_zero, FL_N));
+  TRY(dalloc(h, &h->fl_ir, FL_N));
   TRY(dalloc(h, &h->counter, 4));
   TRY(dalloc(h, &h->status, 4));
   TRY(dalloc(h, &h->U, 2 * (size_t)T.unode_off[T.S]));
@@ -264,6 +278,10 @@ fp_status build_device(fp_handle *h) {
   TRY(dalloc(h, &h->PP, (size_t)T.pnode_off[T.S]));
   CK(cudaMemsetAsync(h->red_counter, 0, 4 * sizeof(unsigned), h->stream));
   CK(cudaMemsetAsync(h->fl_zero, 0, FL_N * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(h->fl_ir, 0, FL_N * sizeof(int), h->stream));
+  // zero every local vector once: kernels write only real rows, so the padding stays zero
+  for (double *v : {h->X2, h->XB, h->XP, h->XY, h->XF, h->XA, h->XR})
+    if (v) CK(cudaMemsetAsync(v, 0, (size_t)nv * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream));
   CK(cudaMemsetAsync(h->lam_prev, 0, nl * sizeof(double), h->stream));
   CK(cudaMallocHost(&h->h_fl, FL_N * sizeof(int)));
@@ -323,6 +341,29 @@ fp_status collect_profile(fp_handle *h) {
   return FP_OK;
 }
 
+// x = K^+ b.  FP64: one solve.  Mixed: FP32 solve then `sweeps` refinement sweeps with the
+// residual b - K_N x in FP64.  b is kept; x must not alias b unless sweeps == 0 and FP64.
+fp_status solve_refined(fp_handle *h, const double *b, double *x, int sweeps, const int *fl) {
+  const long long nv = h->T.vec_off[h->T.S];
+  if (x != b) CK(cudaMemcpyAsync(x, b, nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  TRY(solve_local(h, false, x, fl));
+  if (h->P.precision != FP_PREC_MIXED) return FP_OK;
+  // adaptive: the skip flag fl_ir[FL_IRSKIP] turns the remaining sweeps into no-ops
+  int *skip = h->fl_ir + FL_IRSKIP;
+  CK(cudaMemsetAsync(skip, 0, sizeof(int), h->stream));
+  for (int it = 0; it < sweeps; ++it) {
+    k_residual_N<<<h->T.S, 256, 0, h->stream>>>(h->D, h->csr_val, b, x, h->XR, skip);
+    CKL();
+    TRY(solve_local(h, false, h->XR, skip));
+    k_local_add<<<1184, 256, 0, h->stream>>>(x, h->XR, nv, skip);
+    k_ir_check<<<RED_BLOCKS, 256, 0, h->stream>>>(x, h->XR, nv, h->ir_eps * h->ir_eps, h->partial,
+                                                  h->red_counter + 2, h->fl_ir);
+    CKL();
+  }
+  (void)fl;
+  return FP_OK;
+}
+
 fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
   const int nl = h->T.n_lambda;
   if (!h->T.NF) {
@@ -336,12 +377,21 @@ fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
   return FP_OK;
 }
 
-// out = F v ; leaves K^+ B^T v in XB
-fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl) {
+// out = F v.  accurate: local solves refined to FP64 accuracy (mixed precision); the
+// solution K^+ B^T v is left in xsol(h) (XA for mixed precision, XB for FP64).
+double *xsol(fp_handle *h) { return h->P.precision == FP_PREC_MIXED ? h->XA : h->XB; }
+
+fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, bool accurate = true) {
   k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, v, 1.0, h->XB, 1, fl);
   CKL();
-  TRY(solve_local(h, false, h->XB, fl));
-  k_gather<<<(h->T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->XB, out, fl);
+  double *x = h->XB;
+  if (h->P.precision == FP_PREC_MIXED) {
+    x = h->XA;
+    TRY(solve_refined(h, h->XB, x, accurate ? h->ir_sweeps : h->inner_ir, fl));
+  } else {
+    TRY(solve_local(h, false, x, fl));
+  }
+  k_gather<<<(h->T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, x, out, fl);
   CKL();
   return FP_OK;
 }
@@ -523,6 +573,7 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   const int nl = T.n_lambda;
   const int n = h->step_n + 1;
   const double t_now = n * h->P.tau;
+  const bool mixed = h->P.precision == FP_PREC_MIXED;
   cudaStream_t s = h->stream;
   CK(cudaEventRecord(h->ev[0], s));
   // flags and scalars
@@ -531,10 +582,11 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   const double tol2 = h->P.tol * h->P.tol;
   CK(cudaMemcpyAsync(h->sc + SC_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
-  // right-hand side, d = B K^+ f, e = R^T f
-  k_rhs<<<T.S, 256, 0, s>>>(h->D, h->DP, h->fstat, h->Zn, h->Reta, t_now, h->X2, h->ce);
+  // right-hand side f, d = B K^+ f (refined), e = R^T f
+  double *fbuf = mixed ? h->XF : h->X2;
+  k_rhs<<<T.S, 256, 0, s>>>(h->D, h->DP, h->fstat, h->Zn, h->E0n, h->Reta, t_now, fbuf, h->ce);
   CKL();
-  TRY(solve_local(h, false, h->X2, nullptr));
+  TRY(solve_refined(h, fbuf, h->X2, h->ir_sweeps, nullptr));
   k_gather<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->X2, h->d, nullptr);
   CKL();
   // lambda_00 = G (G^T G)^{-1} e ; lambda_0 = lambda_00 + P lambda^{n-1}
@@ -547,7 +599,7 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   }
   TRY(apply_P(h, h->lam_prev, h->t1, h->fl_zero));
   TRY(lincomb(h, h->lam, h->lam00, 1.0, h->t1, 1.0, nullptr));
-  // reference ||P(d - F lambda_00)||
+  // reference ||P(d - F lambda_00)|| (guess independent)
   if (T.NF) {
     TRY(apply_F(h, h->lam00, h->t2, h->fl_zero));
     TRY(lincomb(h, h->t2, h->d, 1.0, h->t2, -1.0, nullptr));
@@ -556,48 +608,65 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   } else {
     TRY(dot(h, h->d, h->d, OP_STORE, h->sc + SC_REF2, nullptr));
   }
-  // r_0 = P(d - F lambda_0), z_0 = P M^{-1} r_0, p_0 = z_0
+  // r_0 = P(d - F lambda_0) with the accurate operator
   TRY(apply_F(h, h->lam, h->q, h->fl_zero));
   TRY(lincomb(h, h->r, h->d, 1.0, h->q, -1.0, nullptr));
   TRY(apply_P(h, h->r, h->r, h->fl_zero));
-  TRY(dot(h, h->r, h->r, OP_RNORM0, nullptr, nullptr));
-  TRY(apply_M(h, h->r, h->z, h->fl_zero));
-  TRY(apply_P(h, h->z, h->z, h->fl_zero));
-  CK(cudaMemcpyAsync(h->p, h->z, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  TRY(dot(h, h->r, h->z, OP_RZ_INIT, nullptr, nullptr));
   CK(cudaEventRecord(h->ev[1], s));
-  // Algorithm 1 loop; every kernel is a no-op once the device flag `done` is set
-  const int chunk = 8;
-  for (int it = 0; it < h->P.max_it; it += chunk) {
-    for (int c = 0; c < chunk; ++c) {
-      TRY(apply_F(h, h->p, h->q, h->fl));
-      TRY(apply_P(h, h->q, h->q, h->fl));
-      TRY(dot(h, h->p, h->q, OP_PQ, nullptr, h->fl));
-      k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
-      CKL();
-      TRY(apply_M(h, h->r, h->z, h->fl));
-      TRY(apply_P(h, h->z, h->z, h->fl));
-      TRY(dot(h, h->r, h->z, OP_RZ, nullptr, h->fl));
-      k_pcg_pupdate<<<(nl + 255) / 256, 256, 0, s>>>(h->p, h->z, nl, h->sc, h->fl);
-      CKL();
+  // Algorithm 1, restarted from the true residual until the true residual meets tol.
+  // Inside the loop F may use unrefined FP32 solves (mixed precision); every kernel is a
+  // no-op once the device flag `done` is set.
+  int restarts = 0, total_it = 0;
+  for (;;) {
+    TRY(dot(h, h->r, h->r, OP_RNORM0, nullptr, nullptr));
+    TRY(apply_M(h, h->r, h->z, h->fl_zero));
+    TRY(apply_P(h, h->z, h->z, h->fl_zero));
+    CK(cudaMemcpyAsync(h->p, h->z, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(dot(h, h->r, h->z, OP_RZ_INIT, nullptr, nullptr));
+    for (int it = 0; it < h->P.max_it; it += h->pcg_chunk) {
+      for (int c = 0; c < h->pcg_chunk; ++c) {
+        TRY(apply_F(h, h->p, h->q, h->fl, false));
+        TRY(apply_P(h, h->q, h->q, h->fl));
+        TRY(dot(h, h->p, h->q, OP_PQ, nullptr, h->fl));
+        k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
+        CKL();
+        TRY(apply_M(h, h->r, h->z, h->fl));
+        TRY(apply_P(h, h->z, h->z, h->fl));
+        TRY(dot(h, h->r, h->z, OP_RZ, nullptr, h->fl));
+        k_pcg_pupdate<<<(nl + 255) / 256, 256, 0, s>>>(h->p, h->z, nl, h->sc, h->fl);
+        CKL();
+      }
+      CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h->h_fl[FL_DONE]) break;
     }
+    // true residual with the accurate operator; leaves K^+ B^T lambda in xsol(h)
+    TRY(apply_F(h, h->lam, h->t2, h->fl_zero));
+    TRY(lincomb(h, h->t1, h->d, 1.0, h->t2, -1.0, nullptr));
+    TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
+    TRY(dot(h, h->t1, h->t1, OP_STORE, h->sc + SC_TRUE2, nullptr));
     CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (h->h_fl[FL_DONE]) break;
+    total_it = h->h_fl[FL_ITER];
+    const bool ok = h->h_sc[SC_TRUE2] <= tol2 * h->h_sc[SC_REF2];
+    if (ok || h->h_fl[FL_STATUS] || restarts >= h->max_restarts || total_it >= h->P.max_it) break;
+    // restart: r = true residual, keep the iteration count
+    ++restarts;
+    CK(cudaMemcpyAsync(h->r, h->t1, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int zero = 0;
+    CK(cudaMemcpyAsync(h->fl + FL_DONE, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   }
+  h->restarts_last = restarts;
   CK(cudaEventRecord(h->ev[2], s));
-  // recovery: F lambda (leaves K^+ B^T lambda in XB), true residual, alpha, fields
-  TRY(apply_F(h, h->lam, h->t2, h->fl_zero));
-  TRY(lincomb(h, h->t1, h->d, 1.0, h->t2, -1.0, nullptr));
-  TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
-  TRY(dot(h, h->t1, h->t1, OP_STORE, h->sc + SC_TRUE2, nullptr));
+  // recovery: alpha = (G^T G)^{-1} G^T (F lambda - d); x_s = K^+ f - K^+ B^T lambda + R alpha
   if (T.NF) {
     TRY(lincomb(h, h->t1, h->t2, 1.0, h->d, -1.0, nullptr));
     k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr);
     k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->cy, h->calpha, T.nH, nullptr);
     CKL();
   }
-  k_recover<<<T.S, 256, 0, s>>>(h->D, h->DP, h->X2, h->XB, h->calpha, h->U, h->XI, h->ETA, h->PP, h->Reta);
+  k_recover<<<T.S, 256, 0, s>>>(h->D, h->DP, h->X2, xsol(h), h->calpha, h->U, h->XI, h->ETA, h->PP, h->Reta);
   CKL();
   CK(cudaMemcpyAsync(h->lam_prev, h->lam, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaEventRecord(h->ev[3], s));
@@ -609,7 +678,7 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   cudaEventElapsedTime(&ms01, h->ev[0], h->ev[1]);
   cudaEventElapsedTime(&ms12, h->ev[1], h->ev[2]);
   cudaEventElapsedTime(&ms23, h->ev[2], h->ev[3]);
-  h->last_ms[0] = ms01; h->last_ms[1] = ms12; h->last_ms[2] = ms23; h->last_ms[3] = 0;
+  h->last_ms[0] = ms01; h->last_ms[1] = ms12; h->last_ms[2] = ms23; h->last_ms[3] = restarts;
   h->step_n = n;
   const double ref2 = h->h_sc[SC_REF2];
   if (stats) {
@@ -622,7 +691,7 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   if (st) return st;
   if (h->h_fl[FL_STATUS] == DS_BREAKDOWN) { h->err = "PCG breakdown (p^T F p = 0 or non-finite)"; return FP_ERR_BREAKDOWN; }
   if (h->h_fl[FL_STATUS]) { h->err = "non-finite values in PCG"; return FP_ERR_BREAKDOWN; }
-  if (!(h->h_sc[SC_RNORM2] <= tol2 * ref2)) { h->err = "PCG did not converge within max_it"; return FP_ERR_NOT_CONVERGED; }
+  if (!(h->h_sc[SC_TRUE2] <= tol2 * ref2)) { h->err = "PCG did not reach tol within max_it / restarts"; return FP_ERR_NOT_CONVERGED; }
   return FP_OK;
 }
 
@@ -736,6 +805,20 @@ fp_status fp_get_local_matrix(const fp_handle *hc, int s, double *dense) {
 fp_status fp_get_step_timing(const fp_handle *h, double *ms4) {
   if (!h || !ms4) return FP_ERR_INVALID;
   for (int i = 0; i < 4; ++i) ms4[i] = h->last_ms[i];
+  return FP_OK;
+}
+
+fp_status fp_set_option(fp_handle *h, const char *key, double value) {
+  if (!h || !key) return FP_ERR_INVALID;
+  const std::string k(key);
+  const int v = (int)value;
+  auto bad = [&]() { h->err = "fp_set_option: bad value for " + k; return FP_ERR_INVALID; };
+  if (k == "ir_sweeps") { if (v < 0 || v > 16) return bad(); h->ir_sweeps = v; }
+  else if (k == "inner_ir") { if (v < 0 || v > 8) return bad(); h->inner_ir = v; }
+  else if (k == "ir_eps") { if (!(value >= 1e-17) || value > 1e-2) return bad(); h->ir_eps = value; }
+  else if (k == "max_restarts") { if (v < 0 || v > 64) return bad(); h->max_restarts = v; }
+  else if (k == "pcg_chunk") { if (v < 1 || v > 256) return bad(); h->pcg_chunk = v; }
+  else { h->err = "fp_set_option: unknown key " + k; return FP_ERR_INVALID; }
   return FP_OK;
 }
 

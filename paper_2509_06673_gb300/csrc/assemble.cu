@@ -210,8 +210,8 @@ __global__ void k_assemble(DevTopo T, DevParams P, double *csr_val, double *fsta
             val[pos] += v;
           }
         }
-        // loads (manufactured solution only; the point source enters per step)
-        if (P.source == 0) {
+        // loads (manufactured solution; the point source enters per step)
+        if (P.source != 1) {
           double vv[3][2], G[3][2], area;
           tri_vertices(tt, hx, hy, vv);
           bary_grad(vv, G, area);

@@ -68,7 +68,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // PCG state kept on the device: scalar slots, integer flags, reduction finalisers
 enum ScSlot { SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RNORM2, SC_REF2, SC_TOL2, SC_TMP, SC_TRUE2, SC_N = 16 };
-enum FlSlot { FL_DONE = 0, FL_ITER, FL_STATUS, FL_MAXIT, FL_N = 8 };
+enum FlSlot { FL_DONE = 0, FL_ITER, FL_STATUS, FL_MAXIT, FL_IRSKIP, FL_IRSWEEPS, FL_N = 8 };
 enum RedOp { OP_STORE = 0, OP_PQ = 1, OP_RZ_INIT = 2, OP_RZ = 3, OP_RNORM = 4, OP_RNORM0 = 5 };
 constexpr int RED_BLOCKS = 296;  // fixed grid of the two-stage reductions (deterministic)
 

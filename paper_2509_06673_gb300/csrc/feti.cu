@@ -231,6 +231,65 @@ __global__ void k_bnd_apply(DevTopo D, const double *csr_val, const double *y, d
   for (int q = threadIdx.x; q < t.nbnd; q += blockDim.x) xs[bnd[q]] = zsh[q];
 }
 
+// ------------------------------ iterative refinement ---------------------------------
+// r = b - K_N x in FP64 from the assembled CSR values, K_N being K_s with identity rows and
+// columns on the fixed dofs of floating subdomains (the matrix whose factor gives K^+).
+// One CTA per subdomain, one warp per row, fixed-order sums.
+__global__ void k_residual_N(DevTopo D, const double *csr_val, const double *b, const double *x, double *r,
+                             const int *skip) {
+  if (skip && *skip) return;
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long off = D.vec_off[s];
+  const int *cptr = D.pool + t.csr_ptr, *ccol = D.pool + t.csr_col;
+  const double *val = csr_val + D.csr_off[s];
+  auto fixed = [&](int d) { return t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2); };
+  for (int row = warp; row < t.n; row += nw) {
+    if (fixed(row)) {
+      if (lane == 0) r[off + row] = b[off + row] - x[off + row];
+      continue;
+    }
+    double acc = 0.0;
+    for (int e = cptr[row] + lane; e < cptr[row + 1]; e += 32) {
+      const int c = ccol[e];
+      if (!fixed(c)) acc += val[e] * x[off + c];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) r[off + row] = b[off + row] - acc;
+  }
+}
+
+// Refinement stop test: after x += r, skip further sweeps once ||r|| <= eps ||x|| (2-norms
+// over all subdomains).  Counts performed sweeps in fl[FL_IRSWEEPS].
+__global__ void k_ir_check(const double *x, const double *r, long long n, double eps2, double *partial,
+                           unsigned *counter, int *fl) {
+  if (fl[FL_IRSKIP]) return;
+  double sr = 0.0, sx = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    sr += r[i] * r[i];
+    sx += x[i] * x[i];
+  }
+  // two two-stage reductions: ||r||^2 into partial[0, G), ||x||^2 into partial[G, 2G)
+  double tr, tx;
+  finish_reduction(sr, partial, counter, tr);
+  if (finish_reduction(sx, partial + gridDim.x, counter + 1, tx)) {
+    // the block finishing the second reduction re-sums the first partials (all written
+    // before any block's second atomic) in the same fixed order
+    double t1 = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) t1 += ((volatile double *)partial)[i];
+    fl[FL_IRSWEEPS] += 1;
+    if (t1 <= eps2 * tx || !(t1 == t1)) fl[FL_IRSKIP] = 1;
+  }
+}
+
+// x += r over the whole local-vector array
+__global__ void k_local_add(double *x, const double *r, long long n, const int *skip) {
+  if (skip && *skip) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += r[i];
+}
+
 // ------------------------------------ coarse -----------------------------------------
 // y = G^T v : one warp per floating subdomain, lanes stride over its rows, fixed-order sum.
 __global__ void k_Gt(DevTopo D, const double *v, double *y, const int *fl) {
@@ -275,11 +334,12 @@ __global__ void k_Gcomb(DevTopo D, const double *alpha, const double *v, double 
 }
 
 // ------------------------------- right-hand side --------------------------------------
-// f_s at time t: u rows the assembled loads, xi rows 0, p rows -(R eta^{n-1}) - tau Z(t)
+// f_s at time t: u rows the assembled loads (times g(t)), xi rows 0, p rows
+// -(R eta^{n-1}) - tau Z(t)
 // (Eq. (2.42) with eta eliminated).  Writes f into xf (fixed dofs of floating subdomains
 // zeroed, the K^+ convention) and e_f = R_f^T f_f for floating subdomains.
-__global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double *Zn, const double *Reta,
-                      double t_now, double *xf, double *e) {
+__global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double *Zn, const double *E0n,
+                      const double *Reta, double t_now, double *xf, double *e) {
   const int s = blockIdx.x;
   const DevTpl t = D.tpl[D.sub_tpl[s]];
   const double *fs = fstat + D.vec_off[s];
@@ -287,6 +347,8 @@ __global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double 
   const int *dfield = D.pool + t.dof_field, *dnode = D.pool + t.dof_node;
   const long long pn0 = D.pnode_off[s];
   const double q_t = sin(P.q_omega * t_now);
+  // time factor of the time-dependent manufactured variant: g = 1 + t, g' = 1
+  const double g = P.source == 2 ? 1.0 + t_now : 1.0, dg = P.source == 2 ? 1.0 : 0.0;
   const int fidx = D.sub_float[s];
   const double hx = D.sub_hx[s], hy = D.sub_hy[s];
   const double xc = D.sub_x0[s] + 0.5 * t.nx * hx, yc = D.sub_y0[s] + 0.5 * t.ny * hy;
@@ -296,7 +358,7 @@ __global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double 
     const int f = dfield[d], node = dnode[d];
     double v = 0.0;
     if (f <= 1) {
-      v = fs[d];
+      v = g * fs[d];
       if (fidx >= 0) {
         const double xx = D.sub_x0[s] + (node % t.nux) * hx / t.k;
         const double yy = D.sub_y0[s] + (node / t.nux) * hy / t.k;
@@ -304,7 +366,7 @@ __global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double 
         else { e1 += v; e2 += (xx - xc) / L * v; }
       }
     } else if (f == 3) {
-      double z = Zn[pn0 + node];
+      double z = g * Zn[pn0 + node] + dg * E0n[pn0 + node];
       if (P.source == 1 && s == P.src_sub && node == P.src_node) z += q_t;
       v = -Reta[pn0 + node] - P.tau * z;
     }

@@ -370,7 +370,7 @@ bool build_topology(const fp_mesh_desc *m, const fp_params *p, Topology &T, std:
       }
     }
     if (T.src_sub < 0) { err = "point source must lie strictly inside a poroelastic subdomain"; return false; }
-  } else if (p->source != FP_SOURCE_MANUFACTURED) {
+  } else if (p->source != FP_SOURCE_MANUFACTURED && p->source != FP_SOURCE_MANUFACTURED_T) {
     err = "unknown source kind"; return false;
   }
   return true;

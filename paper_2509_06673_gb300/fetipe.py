@@ -22,7 +22,7 @@ FP_OK = 0
 STATUS_NAMES = {0: "FP_OK", 1: "FP_ERR_INVALID", 2: "FP_ERR_OOM", 3: "FP_ERR_CUDA",
                 4: "FP_ERR_NOT_CONVERGED", 5: "FP_ERR_BREAKDOWN", 6: "FP_ERR_TIMEOUT",
                 7: "FP_ERR_STATE"}
-FP_SOURCE_MANUFACTURED, FP_SOURCE_POINT = 0, 1
+FP_SOURCE_MANUFACTURED, FP_SOURCE_POINT, FP_SOURCE_MANUFACTURED_T = 0, 1, 2
 FP_PREC_FP64, FP_PREC_MIXED = 0, 1
 FP_PRECOND_DIRICHLET, FP_PRECOND_NONE = 0, 2
 
@@ -30,7 +30,7 @@ EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_ge
             "fp_get_lambda", "fp_get_lambda_keys", "fp_get_fields", "fp_apply_F",
             "fp_apply_precond", "fp_apply_projection", "fp_apply_projection_noalloc",
             "fp_get_dof_map",
-            "fp_get_local_matrix", "fp_get_step_timing", "fp_set_profiling",
+            "fp_get_local_matrix", "fp_get_step_timing", "fp_set_option", "fp_set_profiling",
             "fp_get_kernel_stats", "fp_last_error", "fp_destroy"]
 
 
@@ -83,6 +83,7 @@ _lib.fp_apply_projection_noalloc.argtypes = [_vp, _vp, _vp]
 _lib.fp_get_dof_map.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int)]
 _lib.fp_get_local_matrix.argtypes = [_vp, ctypes.c_int, _vp]
 _lib.fp_get_step_timing.argtypes = [_vp, _vp]
+_lib.fp_set_option.argtypes = [_vp, ctypes.c_char_p, ctypes.c_double]
 _lib.fp_set_profiling.argtypes = [_vp, ctypes.c_int]
 _lib.fp_get_kernel_stats.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(KernelStats)]
 _lib.fp_last_error.argtypes = [_vp]
@@ -120,7 +121,8 @@ class Solver:
             perm = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in case.perm]))
             self._keep.append(perm)
             perm_ptr = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        src = {"manufactured": FP_SOURCE_MANUFACTURED, "point": FP_SOURCE_POINT}[case.source]
+        src = {"manufactured": FP_SOURCE_MANUFACTURED, "point": FP_SOURCE_POINT,
+               "manufactured_t": FP_SOURCE_MANUFACTURED_T}[case.source]
         prec = precision or case.precision
         par = Params(case.lame_lambda, case.mu, case.alpha, case.c0, case.perm_k, case.mu_f, case.tau,
                      perm_ptr, src, int(case.src_node[0]), int(case.src_node[1]), float(case.q_omega),
@@ -226,6 +228,9 @@ class Solver:
         A = np.empty((f.size, f.size))
         self._check(_lib.fp_get_local_matrix(self._h, s, A.ctypes.data))
         return A
+
+    def set_option(self, key, value):
+        self._check(_lib.fp_set_option(self._h, key.encode(), float(value)))
 
     def set_profiling(self, on=True):
         self._check(_lib.fp_set_profiling(self._h, 1 if on else 0))

@@ -10,6 +10,8 @@ p = 0 on the outer boundary of the poroelastic region):
 
 * ``config1``  1 x 2 subdomains of 16 x 16 cells, P1, lambda = mu = alpha = c0 = K = 1,
                manufactured solution of Test Case 1 (Sec. 4.1), 10 steps of dt = 0.01.
+  Configs 2, 3 and 5 use the same closed form times (1 + t) so that every step changes
+  the solution and the Krylov solve has work to do.
 * ``config2``  8 x 8 subdomains of 32 x 32 cells, P2, nu = 0.49 (lambda = 49, mu = 1),
                50 steps of dt = 1e-3, Dirichlet preconditioner.
 * ``config3``  32 x 32 subdomains, cells per partition column / row uniform on {16..48}
@@ -72,7 +74,7 @@ class Case:
     tau: float = 1e-3
     n_steps: int = 1
     perm: Optional[list] = None          # per subdomain: per-element permeability (or None)
-    source: str = "manufactured"         # "manufactured" | "point" | "barry_mercer"
+    source: str = "manufactured"         # "manufactured" | "manufactured_t" | "point" | "barry_mercer"
     src_node: tuple = (0, 0)             # global P1 grid indices of the point source
     q_omega: float = 0.0
     bc: str = "clamped"                  # "clamped" | "barry_mercer" (oracle only)
@@ -149,7 +151,8 @@ def config1(**kw):
 
 def config2(**kw):
     c = grid_case("config2: 8x8 subdomains, 32x32 cells, P2, nu=0.49", 8, 8, 32, 32,
-                  order_k=2, lame_lambda=lame_from_nu(0.49), tau=1e-3, n_steps=50, tol=1e-10)
+                  order_k=2, lame_lambda=lame_from_nu(0.49), tau=1e-3, n_steps=50, tol=1e-10,
+                  source="manufactured_t")
     return c.with_(**kw)
 
 
@@ -157,7 +160,7 @@ def config3(**kw):
     c = grid_case("config3: 32x32 subdomains, uneven 16..48 cells, P2, nu=0.49", 32, 32,
                   uneven_cells(32, seed=0), uneven_cells(32, seed=0, offset=32),
                   order_k=2, lame_lambda=lame_from_nu(0.49), tau=1e-3, n_steps=100,
-                  tol=1e-8, precision="mixed")
+                  tol=1e-8, precision="mixed", source="manufactured_t")
     return c.with_(**kw)
 
 
@@ -172,7 +175,7 @@ def config4(seed=0, **kw):
 def config5(**kw):
     c = grid_case("config5: 64x64 subdomains, 24x24 cells, P2, nu=0.499, log-normal K", 64, 64,
                   24, 24, order_k=2, lame_lambda=lame_from_nu(0.499), tau=1e-3, n_steps=200,
-                  tol=1e-8, precision="mixed")
+                  tol=1e-8, precision="mixed", source="manufactured_t")
     c = c.with_(perm=lognormal_perm(c, sigma=1.0, seed=0))
     return c.with_(**kw)
 

@@ -1,0 +1,80 @@
+"""Mixed-precision path (FP32 local factors and solves, FP64 outer PCG, coarse problem and
+refinement residuals) against the FP64 oracle.  Bar: 1e-8 relative in lambda, u, xi, eta,
+p, the accuracy target of the mixed arm; the true FP64 interface residual must meet tol.
+The interface tolerance is 1e-13 as in the FP64 tests: the condition number of the
+preconditioned interface operator (up to ~1e3 at lambda = 499) amplifies the residual
+into the field errors."""
+import numpy as np
+import pytest
+
+from paper_2509_06673_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_06673_gb300 import build
+    build.build()
+    from paper_2509_06673_gb300 import fetipe
+    return fetipe
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+CASES = [
+    W.small_case(4, 4, 4, k=2, lame_lambda=49.0, tau=1e-3, n_steps=3, tol=1e-13, precision="mixed",
+                 source="manufactured_t"),
+    W.small_case(4, 4, 6, k=2, lame_lambda=499.0, tau=1e-3, n_steps=2, tol=1e-13, precision="mixed",
+                 source="manufactured_t", perm=None).with_(
+        perm=[np.exp(np.sin(np.arange(72) * (s + 1))) for s in range(16)]),
+    W.grid_case("uneven mixed", 3, 4, [3, 5, 4], [4, 3, 5, 4], order_k=2, lame_lambda=9.0, tau=1e-2,
+                n_steps=2, tol=1e-13, precision="mixed", source="manufactured_t"),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_mixed_steps_match_oracle(F, case):
+    from oracle.monolithic import Discretization, solve_monolithic
+    d = Discretization(case)
+    mono = solve_monolithic(case, d)
+    sol = F.Solver(case)
+    sol.set_option("ir_eps", 1e-15)
+    sol.assemble()
+    sol.factor()
+    for n in range(case.n_steps):
+        st = sol.step()
+        assert st["true_rel_residual"] <= case.tol
+        assert _rel(sol.get_lambda(), mono[n]["lambda"]) < TOL, n
+        fields = F.split_fields(case, *sol.get_fields())
+        for s, (gu, gxi, geta, gp) in enumerate(fields):
+            u, xi, eta, p = mono[n]["fields"][s]
+            assert np.abs(gu - u).max() < TOL * np.abs(u).max(), (n, s)
+            assert np.abs(gxi - xi).max() < TOL * max(np.abs(xi).max(), 1.0), (n, s)
+            if eta is not None:
+                assert np.abs(gp - p).max() < TOL * max(np.abs(p).max(), 1e-300), (n, s)
+                assert np.abs(geta - eta).max() < TOL * max(np.abs(eta).max(), 1e-300), (n, s)
+    sol.close()
+
+
+def test_mixed_operator_accuracy(F):
+    """The refined F apply of the mixed path matches the oracle's FP64 F."""
+    from oracle.monolithic import Discretization
+    from oracle.feti import FETI
+    case = CASES[1]
+    sol = F.Solver(case)
+    sol.assemble()
+    sol.factor()
+    fe = FETI(case, Discretization(case))
+    v = np.random.default_rng(1).normal(size=sol.sizes.n_lambda)
+    assert _rel(sol.apply_F(v), fe.F(v)) < 1e-9
+    sol.set_option("ir_sweeps", 0)
+    e0 = _rel(sol.apply_F(v), fe.F(v))
+    assert 1e-12 < e0 < 1e-2   # plain FP32 solves: visibly less accurate, still close
+    sol.close()

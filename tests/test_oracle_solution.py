@@ -102,3 +102,15 @@ def test_barry_mercer_no_oscillation():
             for st in solve_monolithic(c, d):
                 p = st["fields"][0][3]
                 assert p.min() >= -1e-9 * np.abs(p).max()
+
+
+@pytest.mark.parametrize("k,umin,pmin", [(1, 1.85, 1.75), (2, 2.75, 1.85)])
+def test_time_dependent_variant_orders(k, umin, pmin):
+    """Closed form times (1 + t): backward Euler is exact in time, so the spatial orders of
+    the stationary case are kept."""
+    e = []
+    for N in (8, 16, 32):
+        c = W.grid_case("t", 1, 2, N, N // 2, order_k=k, tau=0.05, n_steps=3, source="manufactured_t")
+        d = Discretization(c)
+        e.append(linf_l2(c, d, solve_monolithic(c, d)))
+    assert np.log2(e[1][0] / e[2][0]) > umin and np.log2(e[1][1] / e[2][1]) > pmin
