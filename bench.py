@@ -28,9 +28,20 @@ sys.path.insert(0, ROOT)
 METRIC = "time steps/s at lambda rel. residual 1e-8"
 
 
+def config5s():
+    """Profiling case: the subdomains and physics of config 5 on a 16 x 16 partition
+    (256 subdomains, about 3 GB of FP32 factors: larger than L2, small enough for ncu)."""
+    from paper_2509_06673_gb300 import workloads as W
+    c = W.config5().with_(perm=None)
+    c = W.grid_case("config5s: 16x16 subdomains of config 5 (24x24 cells, P2, nu=0.499, log-normal K)",
+                    16, 16, 24, 24, order_k=2, lame_lambda=c.lame_lambda, tau=c.tau, tol=c.tol,
+                    precision="mixed", source="manufactured_t")
+    return c.with_(perm=W.lognormal_perm(c, sigma=1.0, seed=0))
+
+
 def workload(name, precision=None):
     from paper_2509_06673_gb300 import workloads as W
-    cfg = {"config2": W.config2, "config3": W.config3, "config5": W.config5}[name]()
+    cfg = {"config2": W.config2, "config3": W.config3, "config5": W.config5, "config5s": config5s}[name]()
     cfg = cfg.with_(tol=1e-8, max_it=2000)
     if precision:
         cfg = cfg.with_(precision=precision)
@@ -181,9 +192,10 @@ def run_native(args):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    its = []
+    its, restarts = [], []
     for _ in range(args.steps):
         its.append(sol.step()["iterations"])
+        restarts.append(int(sol.step_timing()[3]))
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -238,7 +250,7 @@ def run_native(args):
             "config": {"workload": case.name, "precision": case.precision, "tol": case.tol,
                        "subdomains": case.nsub, "n_lambda": s.n_lambda, "dofs": s.n_dofs,
                        "factor_gb": s.factor_bytes / 1e9, "l2": "inputs larger than L2 (factors %.1f GB)"
-                       % (s.factor_bytes / 1e9), "setup_s": setup_s, "pcg_iterations": its,
+                       % (s.factor_bytes / 1e9), "setup_s": setup_s, "pcg_iterations": its, "pcg_restarts": restarts,
                        "parallelism": "replicas (one independent problem per GPU)"},
             "roofline": roof, "clocks": clk,
             "e2e": {"value": world * args.steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 0,
@@ -264,7 +276,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--config", default="config2", choices=["config2", "config3", "config5"])
+    ap.add_argument("--config", default="config2", choices=["config2", "config3", "config5", "config5s"])
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
