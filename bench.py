@@ -174,6 +174,9 @@ def run_native(args):
     case = workload(args.config, args.precision)
     stream = torch.cuda.current_stream()
     sol = F.Solver(case, stream=stream.cuda_stream)
+    for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk)):
+        if val is not None:
+            sol.set_option(key, val)
     t0 = time.perf_counter()
     sol.assemble()
     sol.factor()
@@ -234,12 +237,12 @@ def run_native(args):
         ach = kN["flops_per_launch"] / (avg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_band_solve<double>", "peak_source": "nominal FP64 rate (derived)",
+                "kernel": "k_band_solve_blk<double>" if args.solve_kernel != 0 else "k_band_solve<double>", "peak_source": "nominal FP64 rate (derived)",
                 "achieved_gbs": kN["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9}
     else:
         ach = kN["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": "k_band_solve<float>", "peak_source": src + " (burst copy)"}
+                "traffic": None, "kernel": "k_band_solve_blk<float>" if args.solve_kernel != 0 else "k_band_solve<float>", "peak_source": src + " (burst copy)"}
     roof.update({"launches": launches, "avg_launch_ms": avg_ms,
                  "share_of_step": (kN["total_ms"] + kD["total_ms"]) / ms})
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -279,6 +282,9 @@ def main():
     ap.add_argument("--config", default="config2", choices=["config2", "config3", "config5", "config5s"])
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-kernel", type=int, default=None, help="1 blocked sweeps, 0 row-step sweeps")
+    ap.add_argument("--wpc", type=int, default=None, help="warps per CTA of the local solves")
+    ap.add_argument("--chunk", type=int, default=None, help="bytes per shared-memory stage of the solves")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

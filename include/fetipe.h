@@ -206,7 +206,11 @@ fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
  *   "ir_eps"       [1e-13] refinement stops once ||dx||_2 <= ir_eps ||x||_2 (all subdomains)
  *   "inner_ir"     [0]  refinement sweeps of the local solves inside the PCG loop, 0..8
  *   "max_restarts" [8]  restarts of PCG from the true residual, 0..64
- *   "pcg_chunk"    [8]  PCG iterations launched between two host polls of the stop flag, 1..256 */
+ *   "pcg_chunk"    [8]  PCG iterations launched between two host polls of the stop flag, 1..256
+ *   "solve_kernel" [1]  local solve kernel: 1 blocked sweeps (32-row blocks, inverse diagonal
+ *                       blocks), 0 row-step sweeps
+ *   "solve_wpc"    [0]  warps per CTA of the local solves, 1..8 (0: chosen from the task count)
+ *   "solve_chunk"  [8192] bytes per shared-memory stage of the blocked solves, 4096..65536 */
 fp_status fp_set_option(fp_handle *h, const char *key, double value);
 
 /* Per-kernel-class timing (CUDA events on the handle's stream around every launch of the

@@ -21,6 +21,11 @@ cudaError_t launch_band_factor(bool fp32, const BandTask *tasks, int ntask, void
                                size_t smem, cudaStream_t stream);
 cudaError_t launch_band_solve(bool fp32, int mmax, int grid, int wpc, cudaStream_t stream, const BandTask *tasks,
                               int ntask, const void *fac, double *x, int *counter, int *status, const int *done);
+cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int chunk, cudaStream_t stream,
+                                  const BandTask *tasks, int ntask, const void *fac, const void *linv, double *x,
+                                  int *counter, int *status, const int *done);
+cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
+                             cudaStream_t stream);
 __global__ void k_dot(const double *, const double *, long long, double *, unsigned *, double *, int *, int,
                       double *, int);
 __global__ void k_pcg_update(double *, double *, const double *, const double *, long long, double *, unsigned *,
@@ -64,7 +69,12 @@ struct fp_handle {
   DevParams DP{};
   // matrices
   double *csr_val = nullptr, *fstat = nullptr, *Zn = nullptr, *E0n = nullptr, *Reta = nullptr;
-  void *facN = nullptr, *facD = nullptr;
+  void *facN = nullptr, *facD = nullptr, *linvN = nullptr, *linvD = nullptr;
+  double *linvH = nullptr;
+  long long linv_total = 0;
+  int solve_kernel = 1;    // 1: blocked sweeps with inverse diagonal blocks, 0: row-step sweeps
+  int solve_wpc = 0;       // warps per CTA of the solve kernels (0: automatic)
+  int solve_chunk = 8192;  // bytes per ring stage of the blocked solve
   double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
   BandTask *tasksN = nullptr, *tasksD = nullptr, *taskH = nullptr, *tasksHinv = nullptr;
   int ntask = 0, mmax = 4, mmaxH = 4, ldmax = 32;
@@ -224,11 +234,14 @@ fp_status build_device(fp_handle *h) {
     const Template &ta = T.tpl[T.sub_tpl[a]], &tb = T.tpl[T.sub_tpl[b]];
     return (long long)ta.n * ta.LD > (long long)tb.n * tb.LD;
   });
+  std::vector<long long> linv_off(T.S + 1, 0);
+  for (int s = 0; s < T.S; ++s) linv_off[s + 1] = linv_off[s] + 1024LL * ((T.tpl[T.sub_tpl[s]].n + 31) / 32);
+  h->linv_total = linv_off[T.S];
   std::vector<BandTask> tk;
   int mmax = 1;
   for (int s : order) {
     const Template &t = T.tpl[T.sub_tpl[s]];
-    tk.push_back({T.fac_off[s], T.vec_off[s], t.n, t.LD, t.b, 0});
+    tk.push_back({T.fac_off[s], T.vec_off[s], linv_off[s], t.n, t.LD, t.b, 0});
     mmax = std::max(mmax, t.LD / 32);
   }
   if (mmax > 16) { h->err = "half bandwidth above 511 is not supported"; return FP_ERR_INVALID; }
@@ -239,11 +252,11 @@ fp_status build_device(fp_handle *h) {
   h->tasksN = const_cast<BandTask *>(dt);
   h->tasksD = h->tasksN;  // same offsets; the two factors live in separate arrays
   if (T.NF) {
-    std::vector<BandTask> th = {{0, 0, T.nH, T.LDH, T.bH, 0}};
+    std::vector<BandTask> th = {{0, 0, 0, T.nH, T.LDH, T.bH, 0}};
     TRY(upload(h, &dt, th));
     h->taskH = const_cast<BandTask *>(dt);
     std::vector<BandTask> ti(T.nH);
-    for (int i = 0; i < T.nH; ++i) ti[i] = {0, (long long)i * T.nH, T.nH, T.LDH, T.bH, 0};
+    for (int i = 0; i < T.nH; ++i) ti[i] = {0, (long long)i * T.nH, 0, T.nH, T.LDH, T.bH, 0};
     TRY(upload(h, &dt, ti));
     h->tasksHinv = const_cast<BandTask *>(dt);
     const int mh = T.LDH / 32;
@@ -291,12 +304,29 @@ fp_status build_device(fp_handle *h) {
 }
 
 // ------------------------------ building blocks -------------------------------------
-fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac, double *x,
-                       int mmax, const int *done) {
-  const int wpc = ntask >= 4 * h->num_sms ? 4 : (ntask >= 2 * h->num_sms ? 2 : 1);
-  const int grid = std::max(1, std::min(h->num_sms, (ntask + wpc - 1) / wpc));
+fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac, const void *linv,
+                       double *x, int mmax, const int *done) {
   CK(cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream));
-  CK(launch_band_solve(fp32, mmax, grid, wpc, h->stream, tasks, ntask, fac, x, h->counter, h->status, done));
+  if (h->solve_kernel == 1 && linv) {
+    // stage size: at least one inverse block and one column of the widest band
+    const int esz = fp32 ? 4 : 8;
+    int chunk = std::max(h->solve_chunk, 1024 * esz);
+    chunk = std::max(chunk, (std::max(h->ldmax, h->T.LDH) * esz + 1023) / 1024 * 1024);
+    int wpc = h->solve_wpc;
+    if (wpc <= 0) {
+      wpc = 1;
+      while (wpc < 8 && ntask >= 2 * wpc * h->num_sms) wpc *= 2;
+    }
+    while (wpc > 1 && (size_t)wpc * 3 * (chunk + 8) > 200 * 1024) wpc >>= 1;
+    const int grid = std::max(1, std::min(h->num_sms, (ntask + wpc - 1) / wpc));
+    CK(launch_band_solve_blk(fp32, mmax, grid, wpc, chunk, h->stream, tasks, ntask, fac, linv, x, h->counter,
+                             h->status, done));
+  } else {
+    int wpc = ntask >= 4 * h->num_sms ? 4 : (ntask >= 2 * h->num_sms ? 2 : 1);
+    if (h->solve_wpc > 0) wpc = std::min(h->solve_wpc, 4);
+    const int grid = std::max(1, std::min(h->num_sms, (ntask + wpc - 1) / wpc));
+    CK(launch_band_solve(fp32, mmax, grid, wpc, h->stream, tasks, ntask, fac, x, h->counter, h->status, done));
+  }
   return FP_OK;
 }
 
@@ -320,7 +350,8 @@ fp_status solve_local(fp_handle *h, bool dirichlet, double *x, const int *done) 
     TRY(next_event(h, &e1));
     CK(cudaEventRecord(e0, h->stream));
   }
-  TRY(launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, x, h->mmax, done));
+  const void *linv = dirichlet ? h->linvD : h->linvN;
+  TRY(launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, linv, x, h->mmax, done));
   if (h->profiling) CK(cudaEventRecord(e1, h->stream));
   return FP_OK;
 }
@@ -331,7 +362,7 @@ fp_status collect_profile(fp_handle *h) {
   for (auto &pr : h->pending) {
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]));
-    if (ms > 0.002f) {
+    if (ms > 0.02f) {
       h->prof_launches[pr.first] += 1;
       h->prof_ms[pr.first] += ms;
     }
@@ -436,9 +467,12 @@ fp_status factor_T(fp_handle *h) {
   const size_t nf = (size_t)Tp.fac_off[Tp.S];
   T *fN = nullptr, *fD = nullptr;
   if (!h->facN) {
+    T *lN = nullptr, *lD = nullptr;
     TRY(dalloc(h, &fN, nf));
     TRY(dalloc(h, &fD, nf));
-    h->facN = fN; h->facD = fD;
+    TRY(dalloc(h, &lN, (size_t)h->linv_total));
+    TRY(dalloc(h, &lD, (size_t)h->linv_total));
+    h->facN = fN; h->facD = fD; h->linvN = lN; h->linvD = lD;
   }
   fN = (T *)h->facN; fD = (T *)h->facD;
   const bool f32 = sizeof(T) == 4;
@@ -449,6 +483,8 @@ fp_status factor_T(fp_handle *h) {
   const size_t smem = (size_t)NB * (h->ldmax + 1) * sizeof(T);
   CK(launch_band_factor(f32, h->tasksN, h->ntask, fN, NB, h->status, smem, h->stream));
   CK(launch_band_factor(f32, h->tasksD, h->ntask, fD, NB, h->status, smem, h->stream));
+  CK(launch_band_linv(f32, h->tasksN, h->ntask, fN, h->linvN, h->stream));
+  CK(launch_band_linv(f32, h->tasksD, h->ntask, fD, h->linvD, h->stream));
   return FP_OK;
 }
 
@@ -458,6 +494,7 @@ fp_status factor_coarse(fp_handle *h) {
   if (!h->Hband) {
     TRY(dalloc(h, &h->Hband, (size_t)T.nH * T.LDH));
     TRY(dalloc(h, &h->Hinv, (size_t)T.nH * T.nH));
+    TRY(dalloc(h, &h->linvH, 1024 * (size_t)((T.nH + 31) / 32)));
   }
   k_coarse_G<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->ga, h->gb);
   CK(cudaMemsetAsync(h->Hband, 0, (size_t)T.nH * T.LDH * sizeof(double), h->stream));
@@ -469,7 +506,8 @@ fp_status factor_coarse(fp_handle *h) {
   CK(launch_band_factor(false, h->taskH, 1, h->Hband, NB, h->status, smem, h->stream));
   k_identity<<<1024, 256, 0, h->stream>>>(h->Hinv, T.nH);
   CKL();
-  TRY(launch_solve(h, false, h->tasksHinv, T.nH, h->Hband, h->Hinv, h->mmaxH, nullptr));
+  CK(launch_band_linv(false, h->taskH, 1, h->Hband, h->linvH, h->stream));
+  TRY(launch_solve(h, false, h->tasksHinv, T.nH, h->Hband, h->linvH, h->Hinv, h->mmaxH, nullptr));
   return FP_OK;
 }
 
@@ -818,6 +856,9 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "ir_eps") { if (!(value >= 1e-17) || value > 1e-2) return bad(); h->ir_eps = value; }
   else if (k == "max_restarts") { if (v < 0 || v > 64) return bad(); h->max_restarts = v; }
   else if (k == "pcg_chunk") { if (v < 1 || v > 256) return bad(); h->pcg_chunk = v; }
+  else if (k == "solve_kernel") { if (v < 0 || v > 1) return bad(); h->solve_kernel = v; }
+  else if (k == "solve_wpc") { if (v < 0 || v > 8) return bad(); h->solve_wpc = v; }
+  else if (k == "solve_chunk") { if (v < 4096 || v > 65536 || v % 1024) return bad(); h->solve_chunk = v; }
   else { h->err = "fp_set_option: unknown key " + k; return FP_ERR_INVALID; }
   return FP_OK;
 }

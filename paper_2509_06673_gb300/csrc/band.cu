@@ -152,6 +152,21 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 }  // namespace
 
+// Opaque select: keeps a register-array pick such as "xw[M - 1]" from being folded into a
+// dynamically indexed (local-memory) access.
+__device__ __forceinline__ float opaque_sel(bool p, float a, float b) {
+  float r;
+  asm("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n selp.f32 %0, %1, %2, q;\n}\n"
+      : "=f"(r) : "f"(a), "f"(b), "r"((unsigned)p));
+  return r;
+}
+__device__ __forceinline__ double opaque_sel(bool p, double a, double b) {
+  double r;
+  asm("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n selp.f64 %0, %1, %2, q;\n}\n"
+      : "=d"(r) : "d"(a), "d"(b), "r"((unsigned)p));
+  return r;
+}
+
 constexpr int SOLVE_STAGES = 3;
 constexpr int CHUNK_BYTES = 16384;
 
@@ -277,11 +292,10 @@ __global__ void __launch_bounds__(128) k_band_solve(const BandTask *tasks, int n
       if (abort) break;
       if (j0 + lane < n) x[j0 + lane] = double(zout);
       const T t0 = w[0];
+      // rotate the window by one slot group (select form keeps w in registers)
 #pragma unroll
-      for (int m = 0; m < MMAX; ++m) {
-        if (m < M - 1) w[m] = w[(m + 1 < MMAX) ? m + 1 : m];
-        else if (m == M - 1) w[m] = t0;
-      }
+      for (int m = 0; m + 1 < MMAX; ++m) w[m] = opaque_sel(m < M - 1, w[m + 1], opaque_sel(m == M - 1, t0, w[m]));
+      if (M == MMAX) w[MMAX - 1] = t0;
     }
     if (abort) break;
     release_req(cur);
@@ -324,13 +338,13 @@ __global__ void __launch_bounds__(128) k_band_solve(const BandTask *tasks, int n
       }
       if (abort) break;
       if (j0 + lane < n) x[j0 + lane] = double(xout);
+      // rotate the window back by one slot group; registers m >= M are never read, so the
+      // shift is unconditional (keeps xw in registers)
       T tl = xw[0];
 #pragma unroll
-      for (int m = 1; m < MMAX; ++m)
-        if (m == M - 1) tl = xw[m];
+      for (int m = 1; m < MMAX; ++m) tl = opaque_sel(m == M - 1, xw[m], tl);
 #pragma unroll
-      for (int m = MMAX - 1; m >= 1; --m)
-        if (m < M) xw[m] = xw[m - 1];
+      for (int m = MMAX - 1; m >= 1; --m) xw[m] = xw[m - 1];
       xw[0] = tl;
     }
     if (abort) break;
@@ -356,6 +370,253 @@ FP_SOLVE_INST(float, 4)
 FP_SOLVE_INST(float, 8)
 FP_SOLVE_INST(float, 12)
 FP_SOLVE_INST(float, 16)
+
+// ============================ blocked sweeps ===========================================
+// Inverse of every unit-lower 32 x 32 diagonal block of L, in FP64 from the stored factor,
+// stored row-major (Linv[r][c], zero above the diagonal; identity beyond row n - 1 of a
+// partial last block).  One CTA per task, one warp per block, lane c computes column c by
+// forward substitution x_r = [r == c] - sum_{k<r} L[r][k] x_k.
+template <typename T>
+__global__ void k_band_linv(const BandTask *tasks, int ntask, const T *fbase, T *lbase) {
+  const int task = blockIdx.x;
+  if (task >= ntask) return;
+  const BandTask tk = tasks[task];
+  const T *fac = fbase + tk.fac_off;
+  T *linv = lbase + tk.linv_off;
+  const int n = tk.n, LD = tk.LD, b = tk.b;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nblk = (n + 31) / 32;
+  for (int q = warp; q < nblk; q += nw) {
+    const int j0 = 32 * q, nb = min(32, n - j0);
+    double x[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      double acc = (r == lane) ? 1.0 : 0.0;
+      if (r < nb) {
+#pragma unroll
+        for (int k = 0; k < r; ++k) {
+          const double l = (r - k <= b) ? double(fac[(long long)(j0 + k) * LD + (j0 + r) % LD]) : 0.0;
+          acc -= l * x[k];
+        }
+      }
+      x[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) linv[(long long)q * 1024 + r * 32 + lane] = T(x[r]);
+  }
+}
+
+// Per-warp request stream of the blocked solve: forward [Linv_q, column chunks of block q],
+// backward [column chunks of block q (descending), Linv_q].  Request q of the warp lives in
+// ring stage q % SOLVE_STAGES and completes phase (q / SOLVE_STAGES) & 1 of its mbarrier.
+template <typename T>
+struct BlkStream {
+  unsigned char *ring;
+  uint64_t *bar;
+  const T *fac, *linv;
+  int chunk;                 // bytes per ring stage
+  int n, LD, C, nblk, total;
+  uint32_t seq, issued, seq_task;
+  int idir, iq, ik;  // issue cursor (meaningful in lane 0)
+  bool abort;
+  __device__ __forceinline__ int cpb(int q) const { return (min(32, n - 32 * q) + C - 1) / C; }
+  __device__ __forceinline__ void issue_one() {
+    const int st = issued % SOLVE_STAGES;
+    const void *src;
+    uint32_t bytes;
+    if (ik < 0) {
+      src = linv + (long long)iq * 1024;
+      bytes = 1024 * sizeof(T);
+    } else {
+      const int c0 = 32 * iq + ik * C;
+      src = fac + (long long)c0 * LD;
+      bytes = (uint32_t)min(C, n - c0) * LD * sizeof(T);
+    }
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_g2s(ring + (size_t)st * chunk, src, bytes, &bar[st]);
+    ++issued;
+    if (idir == 0) {
+      if (ik + 1 < cpb(iq)) ++ik;
+      else if (iq + 1 < nblk) { ++iq; ik = -1; }
+      else { idir = 1; iq = nblk - 1; ik = cpb(iq) - 1; }
+    } else {
+      if (ik >= 0) --ik;
+      else if (iq > 0) { --iq; ik = cpb(iq) - 1; }
+      else idir = 2;
+    }
+  }
+  __device__ __forceinline__ void top_up(int lane) {
+    if (lane == 0)
+      while ((int)(issued - seq_task) < total && issued - seq < SOLVE_STAGES) issue_one();
+    issued = __shfl_sync(FULL, issued, 0);
+  }
+  __device__ __forceinline__ const T *acquire() {
+    const bool ok = mbar_wait(&bar[seq % SOLVE_STAGES], (seq / SOLVE_STAGES) & 1);
+    if (!__all_sync(FULL, ok)) { abort = true; return nullptr; }
+    return reinterpret_cast<const T *>(ring + (size_t)(seq % SOLVE_STAGES) * chunk);
+  }
+  __device__ __forceinline__ void release(int lane) {
+    __syncwarp();
+    ++seq;
+    if (lane == 0) fence_proxy_async();
+    top_up(lane);
+  }
+};
+
+template <typename T, int MMAX>
+__global__ void __launch_bounds__(256, 1) k_band_solve_blk(const BandTask *tasks, int ntask, const T *fbase,
+                                                        const T *lbase, double *xbase, int *counter, int *status,
+                                                        const int *done, int chunk) {
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  extern __shared__ __align__(128) unsigned char smem[];
+  BlkStream<T> S;
+  S.chunk = chunk;
+  S.ring = smem + (size_t)warp * SOLVE_STAGES * chunk;
+  S.bar = reinterpret_cast<uint64_t *>(smem + (size_t)nwarps * SOLVE_STAGES * chunk) + warp * SOLVE_STAGES;
+  if (lane == 0)
+    for (int st = 0; st < SOLVE_STAGES; ++st) mbar_init(&S.bar[st], 1);
+  fence_mbar_init();
+  __syncwarp();
+  S.seq = 0;
+  S.issued = 0;
+  S.abort = false;
+  while (!S.abort) {
+    int task = 0;
+    if (lane == 0) task = atomicAdd(counter, 1);
+    task = __shfl_sync(FULL, task, 0);
+    if (task >= ntask) break;
+    const BandTask tk = tasks[task];
+    S.fac = fbase + tk.fac_off;
+    S.linv = lbase + tk.linv_off;
+    double *x = xbase + tk.x_off;
+    const int n = tk.n, LD = tk.LD, M = LD / 32;
+    int C = 32;
+    while (C > 1 && C * LD * (int)sizeof(T) > chunk) C >>= 1;
+    const int nblk = (n + 31) / 32;
+    S.n = n; S.LD = LD; S.C = C; S.nblk = nblk;
+    S.total = 0;
+    for (int q = 0; q < nblk; ++q) S.total += 1 + S.cpb(q);
+    S.total *= 2;
+    S.seq_task = S.seq;
+    S.idir = 0; S.iq = 0; S.ik = -1;
+    S.top_up(lane);
+    // ------------------------------- forward ------------------------------------
+    T w[MMAX];
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m) {
+      const int row = m * 32 + lane;
+      w[m] = (m < M && row < n) ? T(x[row]) : T(0);
+    }
+    for (int q = 0; q < nblk; ++q) {
+      const int j0 = 32 * q, g = q % M;
+      int offs[MMAX];
+#pragma unroll
+      for (int m = 0; m < MMAX; ++m) offs[m] = (m < M) ? ((g + m) % M) * 32 + lane : 0;
+      const int rr = j0 + LD + lane;
+      const T refill = rr < n ? T(x[rr]) : T(0);
+      // y_J = Linv_q w_J (rotated order: conflict-free shared-memory reads)
+      const T *Ls = S.acquire();
+      if (S.abort) break;
+      T y0 = T(0), y1 = T(0);
+#pragma unroll 4
+      for (int i = 0; i < 32; i += 2) {
+        const int k0 = (lane + i) & 31, k1 = (lane + i + 1) & 31;
+        y0 += Ls[lane * 32 + k0] * __shfl_sync(FULL, w[0], k0);
+        y1 += Ls[lane * 32 + k1] * __shfl_sync(FULL, w[0], k1);
+      }
+      const T y = y0 + y1;
+      S.release(lane);
+      // rank-32 update of the window with the block's columns
+      T zout = T(0), corr0 = T(0);
+      const int ncol = min(32, n - j0);
+      for (int c0c = 0; c0c < ncol && !S.abort; c0c += C) {
+        if (c0c) S.release(lane);
+        const T *cb = S.acquire();
+        if (S.abort) break;
+        const int cend = min(ncol, c0c + C);
+#pragma unroll 2
+        for (int cc = c0c; cc < cend; ++cc) {
+          const T *col = cb + (size_t)(cc - c0c) * LD;
+          const T yc = __shfl_sync(FULL, y, cc);
+          const T c0 = col[offs[0]];
+          if (lane == cc) zout = y * c0;
+          if (lane < cc) corr0 += c0 * yc;
+#pragma unroll
+          for (int m = 1; m < MMAX; ++m)
+            if (m < M) w[m] -= col[offs[m]] * yc;
+        }
+      }
+      if (S.abort) break;
+      S.release(lane);
+      if (j0 + lane < n) x[j0 + lane] = double(zout);
+      w[0] = refill - corr0;
+      const T t0 = w[0];
+      // rotate the window by one slot group (select form keeps w in registers)
+#pragma unroll
+      for (int m = 0; m + 1 < MMAX; ++m) w[m] = opaque_sel(m < M - 1, w[m + 1], opaque_sel(m == M - 1, t0, w[m]));
+      if (M == MMAX) w[MMAX - 1] = t0;
+    }
+    if (S.abort) break;
+    // ------------------------------- backward -----------------------------------
+    T xw[MMAX];
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m) xw[m] = T(0);
+    for (int q = nblk - 1; q >= 0; --q) {
+      const int j0 = 32 * q, g = q % M;
+      int offs[MMAX];
+#pragma unroll
+      for (int m = 0; m < MMAX; ++m) offs[m] = (m < M) ? ((g + m) % M) * 32 + lane : 0;
+      const T zin = (j0 + lane < n) ? T(x[j0 + lane]) : T(0);
+      const int ncol = min(32, n - j0);
+      T own = T(0);   // lane c ends with sum_{r > j0 + 31} L[r][j0 + c] x_r
+      // chunks in descending order (the request stream), columns in any order inside one
+      for (int kc = (ncol - 1) / C; kc >= 0 && !S.abort; --kc) {
+        if (kc != (ncol - 1) / C) S.release(lane);
+        const T *cb = S.acquire();
+        if (S.abort) break;
+        const int c0c = kc * C, cend = min(ncol, c0c + C);
+#pragma unroll 4
+        for (int cc = c0c; cc < cend; ++cc) {
+          const T *col = cb + (size_t)(cc - c0c) * LD;
+          T sacc = (lane < cc) ? col[offs[0]] * xw[0] : T(0);
+#pragma unroll
+          for (int m = 1; m < MMAX; ++m)
+            if (m < M) sacc += col[offs[m]] * xw[m];
+          sacc = warp_sum(sacc);
+          if (lane == cc) own = sacc;
+        }
+      }
+      if (S.abort) break;
+      S.release(lane);
+      const T t = zin - own;
+      const T *Ls = S.acquire();
+      if (S.abort) break;
+      T xc0 = T(0), xc1 = T(0);
+#pragma unroll 4
+      for (int i = 0; i < 32; i += 2) {
+        xc0 += Ls[i * 32 + lane] * __shfl_sync(FULL, t, i);
+        xc1 += Ls[(i + 1) * 32 + lane] * __shfl_sync(FULL, t, i + 1);
+      }
+      const T xc = xc0 + xc1;
+      S.release(lane);
+      xw[0] = xc;
+      if (j0 + lane < n) x[j0 + lane] = double(xc);
+      // rotate the window back by one slot group; registers m >= M are never read, so the
+      // shift is unconditional (keeps xw in registers)
+      T tl = xw[0];
+#pragma unroll
+      for (int m = 1; m < MMAX; ++m) tl = opaque_sel(m == M - 1, xw[m], tl);
+#pragma unroll
+      for (int m = MMAX - 1; m >= 1; --m) xw[m] = xw[m - 1];
+      xw[0] = tl;
+    }
+  }
+  if (S.abort) {
+    if (lane == 0) set_status(status, DS_TIMEOUT);
+    for (uint32_t q = S.seq; q < S.issued; ++q) mbar_wait(&S.bar[q % SOLVE_STAGES], (q / SOLVE_STAGES) & 1);
+  }
+}
 
 size_t solve_smem_bytes(int warps_per_cta) {
   return (size_t)warps_per_cta * SOLVE_STAGES * CHUNK_BYTES + (size_t)warps_per_cta * SOLVE_STAGES * 8;
@@ -391,6 +652,43 @@ static cudaError_t launch_solve_T(int mmax, int grid, int wpc, cudaStream_t stre
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, 32 * wpc, smem, stream>>>(tasks, ntask, fac, x, counter, status, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_solve_blk_T(int mmax, int grid, int wpc, int chunk, cudaStream_t stream,
+                                      const BandTask *tasks, int ntask, const T *fac, const T *linv, double *x,
+                                      int *counter, int *status, const int *done) {
+  void (*kern)(const BandTask *, int, const T *, const T *, double *, int *, int *, const int *, int) = nullptr;
+  switch (mmax) {
+    case 4: kern = k_band_solve_blk<T, 4>; break;
+    case 8: kern = k_band_solve_blk<T, 8>; break;
+    case 12: kern = k_band_solve_blk<T, 12>; break;
+    default: kern = k_band_solve_blk<T, 16>; break;
+  }
+  const size_t smem = (size_t)wpc * SOLVE_STAGES * (chunk + 8);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 32 * wpc, smem, stream>>>(tasks, ntask, fac, linv, x, counter, status, done, chunk);
+  return cudaGetLastError();
+}
+
+// chunk: bytes per ring stage (multiple of 1024, >= 1024 * sizeof(T) to hold an inverse
+// block and >= one factor column), wpc: warps per CTA (1..8).
+cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int chunk, cudaStream_t stream,
+                                  const BandTask *tasks, int ntask, const void *fac, const void *linv, double *x,
+                                  int *counter, int *status, const int *done) {
+  if (fp32)
+    return launch_solve_blk_T<float>(mmax, grid, wpc, chunk, stream, tasks, ntask, (const float *)fac,
+                                     (const float *)linv, x, counter, status, done);
+  return launch_solve_blk_T<double>(mmax, grid, wpc, chunk, stream, tasks, ntask, (const double *)fac,
+                                    (const double *)linv, x, counter, status, done);
+}
+
+cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
+                             cudaStream_t stream) {
+  if (fp32) k_band_linv<float><<<ntask, 256, 0, stream>>>(tasks, ntask, (const float *)fac, (float *)linv);
+  else k_band_linv<double><<<ntask, 256, 0, stream>>>(tasks, ntask, (const double *)fac, (double *)linv);
   return cudaGetLastError();
 }
 

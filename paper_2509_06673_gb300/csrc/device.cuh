@@ -52,6 +52,7 @@ struct DevParams {
 struct BandTask {
   long long fac_off;   // element offset of the factor
   long long x_off;     // element offset of the vector
+  long long linv_off;  // element offset of the inverse diagonal 32 x 32 blocks
   int n, LD, b, pad;
 };
 
