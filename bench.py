@@ -266,6 +266,27 @@ def run_native(args):
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": info["cores"], "kind": "oracle",
                                 "sample": info["sample"]}
     sol.close()
+    del sol
+    if not args.no_fp64_arm and case.precision != "fp64":
+        # the comparison arm of the metric: plain FP64 FETI on the same workload
+        c64 = case.with_(precision="fp64")
+        s64 = F.Solver(c64, stream=stream.cuda_stream)
+        s64.assemble()
+        s64.factor()
+        for _ in range(args.warmup):
+            s64.step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its64 = [s64.step()["iterations"] for _ in range(args.fp64_steps)]
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1)
+        line["fp64_arm"] = {"value": world * args.fp64_steps / (ms64 / 1000.0), "unit": "steps/s",
+                            "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps,
+                            "pcg_iterations": its64,
+                            "speedup_of_value": value / (world * args.fp64_steps / (ms64 / 1000.0))}
+        s64.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -279,7 +300,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--config", default="config2", choices=["config2", "config3", "config5", "config5s"])
+    ap.add_argument("--config", default="config5", choices=["config2", "config3", "config5", "config5s"])
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 comparison arm")
+    ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-kernel", type=int, default=None, help="1 blocked sweeps, 0 row-step sweeps")
