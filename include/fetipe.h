@@ -112,6 +112,9 @@ typedef struct {
   int iterations;            /* PCG iterations */
   double rel_residual;       /* recursive ||P r|| / ||P(d - F lambda_00)|| at exit */
   double true_rel_residual;  /* the same with r recomputed from lambda at exit */
+  int lambda0_learned;       /* 1 if the learned initial guess won the judge this step */
+  double guess_res_prev;     /* relative true residual of the lambda^{n-1} guess (-1: not computed) */
+  double guess_res_learned;  /* relative true residual of the learned guess (-1: not computed) */
 } fp_step_stats;
 
 /* Copies the mesh description and parameters, builds the dof numbering, band ordering and
@@ -198,6 +201,33 @@ fp_status fp_get_local_matrix(const fp_handle *h, int s, double *dense);
 /* Device time of the last fp_step split by phase (milliseconds, CUDA events):
  * [0] rhs + d, [1] PCG loop, [2] recovery; [3] total local-solve time of the step. */
 fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
+
+/* ---------------- learned initial guess (not in the paper: a library pattern) ----------
+ * A 3-layer MLP (8 -> 256 -> 256 -> 1, ReLU; the 256 x 256 products on tensor cores with
+ * bfloat16 operands and FP32 accumulation) maps per-multiplier features (the last increment
+ * lambda^{n-1} - lambda^{n-2} and lambda^{n-1}, each divided by its RMS; the ratio rho of the
+ * last two increments of the source's time signal; rho times the first feature; the node
+ * position; kind and component) to a correction of the source-scaled extrapolation: the
+ * predicted increment, in units of the RMS of the last one, is rho * (last increment) + MLP.
+ * With fp_learned_use on, fp_step computes both guesses lambda_00 + P lambda^{n-1} and
+ * lambda_00 + P(lambda^{n-1} + s (x3 + MLP)) and keeps the one with the smaller true projected
+ * residual (the judge); lambda^{n-1} is the fallback.  Parameters: one flat FP32 array of
+ * 68353 values: W1 [8 x 256] row-major, b1 [256], W2 [256 x 256] row-major, b2 [256],
+ * W3 [256], b3 [1]. */
+fp_status fp_learned_record(fp_handle *h, int on, long long max_samples, int per_step);
+fp_status fp_learned_use(fp_handle *h, int on);
+fp_status fp_learned_train(fp_handle *h, int epochs, int batch, double lr, unsigned long long seed,
+                           double *last_loss);
+fp_status fp_learned_num_samples(const fp_handle *h, long long *n);
+/* He-uniform W1, W2 from SplitMix64 stream `seed` (value i -> parameter i); W3 and biases 0. */
+fp_status fp_mlp_init(fp_handle *h, unsigned long long seed);
+fp_status fp_mlp_set_params(fp_handle *h, const float *host, int n);
+fp_status fp_mlp_get_params(const fp_handle *h, float *host, int n);
+/* Forward pass / mean-squared-error loss L = sum((out - y)^2) / (2 rows) and its gradient,
+ * on host arrays of at most 65536 rows (x: rows x 8). */
+fp_status fp_mlp_forward(fp_handle *h, const float *x, int rows, float *out);
+fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int rows, float *grad,
+                           double *loss);
 
 /* Tunables of the solve (defaults in brackets); FP_ERR_INVALID for an unknown key or a value
  * out of range.

@@ -50,6 +50,30 @@ __global__ void k_residual_N(DevTopo, const double *, const double *, const doub
 __global__ void k_local_add(double *, const double *, long long, const int *);
 __global__ void k_ir_check(const double *, const double *, long long, double, double *, unsigned *, int *);
 
+// learned lambda_0 (learned.cu)
+constexpr int MLP_NIN = 8, MLP_NH = 256, MLP_NPARAM = 8 * 256 + 256 + 256 * 256 + 256 + 256 + 1;
+constexpr int MLP_OFF_W2 = 8 * 256 + 256, MLP_OFF_B2 = MLP_OFF_W2 + 256 * 256, MLP_OFF_B1 = 8 * 256;
+constexpr int MLP_OFF_W3 = MLP_OFF_B2 + 256, MLP_OFF_B3 = MLP_OFF_W3 + 256;
+cudaError_t launch_gemm_bf16(cudaStream_t s, int M, int N, int K, const float *A, long long sai, long long sak,
+                             const float *B, long long sbk, long long sbj, float *C, int ldc, const float *bias,
+                             float *z, const float *mask, int relu);
+__global__ void k_mlp_l1(int, const float *, const float *, float *, float *);
+__global__ void k_mlp_l3(int, const float *, const float *, float *, const float *, float *, double *, float);
+__global__ void k_mlp_d2(int, const float *, const float *, const float *, float *);
+__global__ void k_colsum(int, int, const float *, int, const float *, float *);
+__global__ void k_mlp_dw1(int, const float *, const float *, float *);
+__global__ void k_sum_double(const double *, int, double *);
+__global__ void k_adam(float *, const float *, float *, float *, int, float, float, float, float, int);
+__global__ void k_mlp_init(float *, unsigned long long);
+__global__ void k_features(int, const double *, const double *, const double *, double, const float *, const int *,
+                           const int *, float *, float *);
+__global__ void k_guess(int, const double *, const float *, const float *, const double *, double *);
+__global__ void k_record(int, const float *, const double *, const double *, const double *, int, int, long long,
+                         long long, float *, float *);
+__global__ void k_gather_rows(int, const int *, const float *, const float *, float *, float *);
+__global__ void k_choose(int, double *, double *, const double *, const double *, const double *, const double *,
+                         int *);
+
 }  // namespace fp
 
 using namespace fp;
@@ -108,6 +132,22 @@ struct fp_handle {
   long long prof_launches[2] = {0, 0};
   double prof_ms[2] = {0, 0};
   double bytes_per_solve = 0, flops_per_solve = 0;
+  // learned lambda_0
+  static constexpr int CH = 65536;             // rows per MLP chunk / max training batch
+  float *mlpP = nullptr, *mlpG = nullptr, *mlpM1 = nullptr, *mlpM2 = nullptr;
+  float *Xf = nullptr, *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *mout = nullptr, *dout = nullptr,
+        *yb = nullptr, *xb = nullptr, *fscale = nullptr;
+  double *loss_rows = nullptr, *loss_acc = nullptr, *fsum = nullptr, *nrm = nullptr;
+  float *xy_rows = nullptr;
+  int *kind_rows = nullptr, *comp_rows = nullptr, *idx_dev = nullptr, *choose_flag = nullptr;
+  double *lam_prev2 = nullptr, *lam_b = nullptr, *r_b = nullptr;
+  float *SX = nullptr, *SY = nullptr;
+  long long n_samples = 0, cap_samples = 0;
+  int mlp_ready = 0, learned_use = 0, learned_record = 0, adam_step = 0, hist = 0;
+  int record_per_step = 65536;
+  double sigma_hist[2] = {0, 0};               // source signal at t_{n-1}, t_{n-2}
+  int last_learned = 0;
+  double last_res_prev = -1, last_res_learned = -1;
 };
 
 namespace {
@@ -297,6 +337,47 @@ fp_status build_device(fp_handle *h) {
     if (v) CK(cudaMemsetAsync(v, 0, (size_t)nv * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream));
   CK(cudaMemsetAsync(h->lam_prev, 0, nl * sizeof(double), h->stream));
+  // learned lambda_0 state (features per multiplier, MLP chunk buffers)
+  {
+    const int CH = fp_handle::CH;
+    TRY(dalloc(h, &h->mlpP, MLP_NPARAM)); TRY(dalloc(h, &h->mlpG, MLP_NPARAM));
+    TRY(dalloc(h, &h->mlpM1, MLP_NPARAM)); TRY(dalloc(h, &h->mlpM2, MLP_NPARAM));
+    TRY(dalloc(h, &h->Xf, (size_t)nl * MLP_NIN));
+    for (float **v : {&h->z1, &h->h1, &h->z2, &h->h2}) TRY(dalloc(h, v, (size_t)CH * MLP_NH));
+    for (float **v : {&h->mout, &h->dout, &h->yb}) TRY(dalloc(h, v, (size_t)std::max<long long>(CH, nl)));
+    TRY(dalloc(h, &h->xb, (size_t)CH * MLP_NIN));
+    TRY(dalloc(h, &h->fscale, 1));
+    TRY(dalloc(h, &h->loss_rows, CH)); TRY(dalloc(h, &h->loss_acc, 1));
+    TRY(dalloc(h, &h->fsum, 2)); TRY(dalloc(h, &h->nrm, 2));
+    TRY(dalloc(h, &h->idx_dev, CH)); TRY(dalloc(h, &h->choose_flag, 1));
+    for (double **v : {&h->lam_prev2, &h->lam_b, &h->r_b}) TRY(dalloc(h, v, (size_t)nl));
+    CK(cudaMemsetAsync(h->lam_prev2, 0, nl * sizeof(double), h->stream));
+    // node coordinates, kind and component of every multiplier (geometry of the keys)
+    std::vector<float> xy(2 * (size_t)nl, 0.f);
+    std::vector<int> kd(nl, 0), cp(nl, 0);
+    std::vector<double> xs(T.nsx + 1, 0), ys(T.nsy + 1, 0);
+    for (int r = 0; r < T.n_lambda; ++r) {
+      const int kind = T.lam_key[6 * r], comp = T.lam_key[6 * r + 1], I = T.lam_key[6 * r + 2], J = T.lam_key[6 * r + 3];
+      const int kk = kind == 0 ? T.k : 1;
+      auto coord = [&](int G, const std::vector<int> &cells, int nsub) {
+        int base = 0;
+        for (int c = 0; c < nsub; ++c) {
+          const int w = kk * cells[c];
+          if (G <= base + w) return ((double)c + (double)(G - base) / w) / nsub;
+          base += w;
+        }
+        return 1.0;
+      };
+      xy[2 * r] = (float)coord(I, T.cells_x, T.nsx);
+      xy[2 * r + 1] = (float)coord(J, T.cells_y, T.nsy);
+      kd[r] = kind;
+      cp[r] = comp;
+    }
+    const float *dxy = nullptr;
+    const int *dk = nullptr, *dc = nullptr;
+    TRY(upload(h, &dxy, xy)); TRY(upload(h, &dk, kd)); TRY(upload(h, &dc, cp));
+    h->xy_rows = const_cast<float *>(dxy); h->kind_rows = const_cast<int *>(dk); h->comp_rows = const_cast<int *>(dc);
+  }
   CK(cudaMallocHost(&h->h_fl, FL_N * sizeof(int)));
   CK(cudaMallocHost(&h->h_sc, SC_N * sizeof(double)));
   for (auto &e : h->ev) CK(cudaEventCreate(&e));
@@ -461,6 +542,82 @@ fp_status lincomb(fp_handle *h, double *out, const double *x, double a, const do
   return FP_OK;
 }
 
+
+// ------------------------------- learned lambda_0 ------------------------------------
+double source_signal(const fp_handle *h, double t) {
+  if (h->P.source == FP_SOURCE_POINT) return std::sin(h->P.q_omega * t);
+  if (h->P.source == FP_SOURCE_MANUFACTURED_T) return 1.0 + t;
+  return 1.0;
+}
+
+// forward over `rows` feature rows (device X, rows x 8) -> out (device, rows)
+fp_status mlp_forward(fp_handle *h, const float *X, long long rows, float *out) {
+  const int CH = fp_handle::CH;
+  cudaStream_t s = h->stream;
+  for (long long r0 = 0; r0 < rows; r0 += CH) {
+    const int m = (int)std::min<long long>(CH, rows - r0);
+    k_mlp_l1<<<(m * MLP_NH + 255) / 256, 256, 0, s>>>(m, X + r0 * MLP_NIN, h->mlpP, nullptr, h->h1);
+    CK(launch_gemm_bf16(s, m, MLP_NH, MLP_NH, h->h1, MLP_NH, 1, h->mlpP + MLP_OFF_W2, MLP_NH, 1, h->h2, MLP_NH,
+                        h->mlpP + MLP_OFF_B2, nullptr, nullptr, 1));
+    k_mlp_l3<<<(m * 32 + 255) / 256, 256, 0, s>>>(m, h->h2, h->mlpP, out + r0, nullptr, nullptr, nullptr, 0.f);
+    CKL();
+  }
+  return FP_OK;
+}
+
+// loss (accumulated into loss_acc) and gradient (into mlpG) of m <= CH rows
+fp_status mlp_loss_grad(fp_handle *h, const float *X, const float *Y, int m) {
+  cudaStream_t s = h->stream;
+  float *P = h->mlpP, *G = h->mlpG;
+  k_mlp_l1<<<(m * MLP_NH + 255) / 256, 256, 0, s>>>(m, X, P, h->z1, h->h1);
+  CK(launch_gemm_bf16(s, m, MLP_NH, MLP_NH, h->h1, MLP_NH, 1, P + MLP_OFF_W2, MLP_NH, 1, h->h2, MLP_NH,
+                      P + MLP_OFF_B2, h->z2, nullptr, 1));
+  k_mlp_l3<<<(m * 32 + 255) / 256, 256, 0, s>>>(m, h->h2, P, h->mout, Y, h->dout, h->loss_rows, 1.f / m);
+  k_colsum<<<(MLP_NH + 31) / 32, 256, 0, s>>>(m, MLP_NH, h->h2, MLP_NH, h->dout, G + MLP_OFF_W3);
+  k_colsum<<<1, 256, 0, s>>>(m, 1, h->dout, 1, nullptr, G + MLP_OFF_B3);
+  k_mlp_d2<<<(m * MLP_NH + 255) / 256, 256, 0, s>>>(m, h->dout, P, h->z2, h->z2);  // d2 in place of z2
+  k_colsum<<<(MLP_NH + 31) / 32, 256, 0, s>>>(m, MLP_NH, h->z2, MLP_NH, nullptr, G + MLP_OFF_B2);
+  CKL();
+  // dW2 = h1^T d2
+  CK(launch_gemm_bf16(s, MLP_NH, MLP_NH, m, h->h1, 1, MLP_NH, h->z2, MLP_NH, 1, G + MLP_OFF_W2, MLP_NH, nullptr,
+                      nullptr, nullptr, 0));
+  // d1 = (d2 W2^T) * (z1 > 0), into the h2 buffer
+  CK(launch_gemm_bf16(s, m, MLP_NH, MLP_NH, h->z2, MLP_NH, 1, P + MLP_OFF_W2, 1, MLP_NH, h->h2, MLP_NH, nullptr,
+                      nullptr, h->z1, 0));
+  k_colsum<<<(MLP_NH + 31) / 32, 256, 0, s>>>(m, MLP_NH, h->h2, MLP_NH, nullptr, G + MLP_OFF_B1);
+  k_mlp_dw1<<<(MLP_NIN * MLP_NH + 255) / 256, 256, 0, s>>>(m, X, h->h2, G);
+  k_sum_double<<<1, 256, 0, s>>>(h->loss_rows, m, h->loss_acc);
+  CKL();
+  return FP_OK;
+}
+
+fp_status mlp_ensure_init(fp_handle *h, unsigned long long seed) {
+  if (h->mlp_ready) return FP_OK;
+  k_mlp_init<<<(MLP_NPARAM + 255) / 256, 256, 0, h->stream>>>(h->mlpP, seed);
+  CKL();
+  CK(cudaMemsetAsync(h->mlpM1, 0, MLP_NPARAM * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->mlpM2, 0, MLP_NPARAM * sizeof(float), h->stream));
+  h->adam_step = 0;
+  h->mlp_ready = 1;
+  return FP_OK;
+}
+
+// features of step n from lambda^{n-1}, lambda^{n-2} and the source signal; fsum gets the
+// sums of squares of the last increment and of lambda^{n-1}
+fp_status build_features(fp_handle *h, double t_now) {
+  const int nl = h->T.n_lambda;
+  const double s0 = source_signal(h, t_now), s1 = h->sigma_hist[0], s2 = h->sigma_hist[1];
+  double rho = 1.0;
+  if (std::fabs(s1 - s2) > 1e-300) rho = std::max(-4.0, std::min(4.0, (s0 - s1) / (s1 - s2)));
+  TRY(lincomb(h, h->t1, h->lam_prev, 1.0, h->lam_prev2, -1.0, nullptr));
+  TRY(dot(h, h->t1, h->t1, OP_STORE, h->fsum, nullptr));
+  TRY(dot(h, h->lam_prev, h->lam_prev, OP_STORE, h->fsum + 1, nullptr));
+  k_features<<<(nl + 255) / 256, 256, 0, h->stream>>>(nl, h->lam_prev, h->lam_prev2, h->fsum, rho, h->xy_rows,
+                                                      h->kind_rows, h->comp_rows, h->Xf, h->fscale);
+  CKL();
+  return FP_OK;
+}
+
 template <typename T>
 fp_status factor_T(fp_handle *h) {
   Topology &Tp = h->T;
@@ -583,6 +740,9 @@ fp_status fp_assemble(fp_handle *h) {
   // initial state: R eta^0 = (eta_0, phi_i) (L2 projection), lambda^0 = 0
   CK(cudaMemcpyAsync(h->Reta, h->E0n, T.pnode_off[T.S] * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemsetAsync(h->lam_prev, 0, std::max(T.n_lambda, 1) * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->lam_prev2, 0, std::max(T.n_lambda, 1) * sizeof(double), h->stream));
+  h->hist = 0;
+  h->sigma_hist[0] = h->sigma_hist[1] = 0.0;
   CK(cudaMemsetAsync(h->U, 0, 2 * T.unode_off[T.S] * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->XI, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->ETA, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
@@ -650,6 +810,26 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   TRY(apply_F(h, h->lam, h->q, h->fl_zero));
   TRY(lincomb(h, h->r, h->d, 1.0, h->q, -1.0, nullptr));
   TRY(apply_P(h, h->r, h->r, h->fl_zero));
+  // learned lambda_0: the MLP predicts the next increment; the judge keeps whichever guess
+  // has the smaller true projected residual (lambda^{n-1} is the fallback)
+  const bool use_learned = h->learned_use && h->mlp_ready && h->hist >= 2;
+  bool features_built = false;
+  if (use_learned) {
+    TRY(build_features(h, t_now));
+    features_built = true;
+    TRY(mlp_forward(h, h->Xf, nl, h->mout));
+    k_guess<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam_prev, h->mout, h->Xf, h->fsum, h->t2);
+    CKL();
+    TRY(apply_P(h, h->t2, h->t2, h->fl_zero));
+    TRY(lincomb(h, h->lam_b, h->lam00, 1.0, h->t2, 1.0, nullptr));
+    TRY(apply_F(h, h->lam_b, h->q, h->fl_zero));
+    TRY(lincomb(h, h->r_b, h->d, 1.0, h->q, -1.0, nullptr));
+    TRY(apply_P(h, h->r_b, h->r_b, h->fl_zero));
+    TRY(dot(h, h->r, h->r, OP_STORE, h->nrm, nullptr));
+    TRY(dot(h, h->r_b, h->r_b, OP_STORE, h->nrm + 1, nullptr));
+    k_choose<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam, h->r, h->lam_b, h->r_b, h->nrm, h->nrm + 1, h->choose_flag);
+    CKL();
+  }
   CK(cudaEventRecord(h->ev[1], s));
   // Algorithm 1, restarted from the true residual until the true residual meets tol.
   // Inside the loop F may use unrefined FP32 solves (mixed precision); every kernel is a
@@ -706,10 +886,33 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   }
   k_recover<<<T.S, 256, 0, s>>>(h->D, h->DP, h->X2, xsol(h), h->calpha, h->U, h->XI, h->ETA, h->PP, h->Reta);
   CKL();
+  // training samples: features of this step and target (lambda^n - lambda^{n-1}) / s1
+  if (h->learned_record && h->hist >= 2 && h->n_samples < h->cap_samples) {
+    if (!features_built) TRY(build_features(h, t_now));
+    const int per = std::min(h->record_per_step, nl);
+    const int stride = std::max(1, nl / per);
+    const int r0 = (int)(h->step_n % stride);
+    const long long cnt = (nl - r0 + stride - 1) / stride;
+    k_record<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(nl, h->Xf, h->lam, h->lam_prev, h->fsum, r0, stride,
+                                                           h->n_samples, h->cap_samples, h->SX, h->SY);
+    CKL();
+    h->n_samples = std::min(h->cap_samples, h->n_samples + cnt);
+  }
+  // history: lambda^{n-2} <- lambda^{n-1} <- lambda^n
+  CK(cudaMemcpyAsync(h->lam_prev2, h->lam_prev, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->lam_prev, h->lam, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  h->sigma_hist[1] = h->sigma_hist[0];
+  h->sigma_hist[0] = source_signal(h, t_now);
+  h->hist += 1;
   CK(cudaEventRecord(h->ev[3], s));
   CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double hn[2] = {-1, -1};
+  int hflag = 0;
+  if (use_learned) {
+    CK(cudaMemcpyAsync(hn, h->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hflag, h->choose_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
   CK(cudaStreamSynchronize(s));
   TRY(collect_profile(h));
   float ms01 = 0, ms12 = 0, ms23 = 0;
@@ -719,9 +922,15 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   h->last_ms[0] = ms01; h->last_ms[1] = ms12; h->last_ms[2] = ms23; h->last_ms[3] = restarts;
   h->step_n = n;
   const double ref2 = h->h_sc[SC_REF2];
+  h->last_learned = hflag;
+  h->last_res_prev = hn[0] >= 0 && ref2 > 0 ? std::sqrt(hn[0] / ref2) : -1.0;
+  h->last_res_learned = hn[1] >= 0 && ref2 > 0 ? std::sqrt(hn[1] / ref2) : -1.0;
   if (stats) {
     stats->step = n;
     stats->iterations = h->h_fl[FL_ITER];
+    stats->lambda0_learned = hflag;
+    stats->guess_res_prev = h->last_res_prev;
+    stats->guess_res_learned = h->last_res_learned;
     stats->rel_residual = ref2 > 0 ? std::sqrt(h->h_sc[SC_RNORM2] / ref2) : 0.0;
     stats->true_rel_residual = ref2 > 0 ? std::sqrt(h->h_sc[SC_TRUE2] / ref2) : 0.0;
   }
@@ -843,6 +1052,132 @@ fp_status fp_get_local_matrix(const fp_handle *hc, int s, double *dense) {
 fp_status fp_get_step_timing(const fp_handle *h, double *ms4) {
   if (!h || !ms4) return FP_ERR_INVALID;
   for (int i = 0; i < 4; ++i) ms4[i] = h->last_ms[i];
+  return FP_OK;
+}
+
+
+// ------------------------------- learned lambda_0 ABI --------------------------------
+fp_status fp_learned_record(fp_handle *h, int on, long long max_samples, int per_step) {
+  if (!h || max_samples < 0 || per_step < 1) return FP_ERR_INVALID;
+  if (on && max_samples > h->cap_samples) {
+    float *sx = nullptr, *sy = nullptr;
+    TRY(dalloc(h, &sx, (size_t)max_samples * MLP_NIN));
+    TRY(dalloc(h, &sy, (size_t)max_samples));
+    if (h->SX && h->n_samples)
+      CK(cudaMemcpyAsync(sx, h->SX, h->n_samples * MLP_NIN * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->SY && h->n_samples)
+      CK(cudaMemcpyAsync(sy, h->SY, h->n_samples * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    h->SX = sx; h->SY = sy; h->cap_samples = max_samples;
+  }
+  h->learned_record = on ? 1 : 0;
+  h->record_per_step = per_step;
+  return FP_OK;
+}
+
+fp_status fp_learned_use(fp_handle *h, int on) {
+  if (!h) return FP_ERR_INVALID;
+  if (on && !h->mlp_ready) { h->err = "fp_learned_use: the network has no parameters (train or set them)"; return FP_ERR_STATE; }
+  h->learned_use = on ? 1 : 0;
+  return FP_OK;
+}
+
+fp_status fp_learned_num_samples(const fp_handle *h, long long *n) {
+  if (!h || !n) return FP_ERR_INVALID;
+  *n = h->n_samples;
+  return FP_OK;
+}
+
+fp_status fp_mlp_init(fp_handle *h, unsigned long long seed) {
+  if (!h) return FP_ERR_INVALID;
+  h->mlp_ready = 0;
+  TRY(mlp_ensure_init(h, seed));
+  CK(cudaStreamSynchronize(h->stream));
+  return FP_OK;
+}
+
+fp_status fp_mlp_set_params(fp_handle *h, const float *host, int n) {
+  if (!h || !host || n != MLP_NPARAM) return FP_ERR_INVALID;
+  CK(cudaMemcpyAsync(h->mlpP, host, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->mlpM1, 0, MLP_NPARAM * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->mlpM2, 0, MLP_NPARAM * sizeof(float), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->adam_step = 0;
+  h->mlp_ready = 1;
+  return FP_OK;
+}
+
+fp_status fp_mlp_get_params(const fp_handle *hc, float *host, int n) {
+  fp_handle *h = const_cast<fp_handle *>(hc);
+  if (!h || !host || n != MLP_NPARAM) return FP_ERR_INVALID;
+  CK(cudaMemcpyAsync(host, h->mlpP, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FP_OK;
+}
+
+fp_status fp_mlp_forward(fp_handle *h, const float *x, int rows, float *out) {
+  if (!h || !x || !out || rows < 1 || rows > fp_handle::CH) return FP_ERR_INVALID;
+  if (!h->mlp_ready) { h->err = "no MLP parameters"; return FP_ERR_STATE; }
+  CK(cudaMemcpyAsync(h->xb, x, (size_t)rows * MLP_NIN * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  TRY(mlp_forward(h, h->xb, rows, h->mout));
+  CK(cudaMemcpyAsync(out, h->mout, rows * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FP_OK;
+}
+
+fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int rows, float *grad, double *loss) {
+  if (!h || !x || !y || !grad || rows < 1 || rows > fp_handle::CH) return FP_ERR_INVALID;
+  if (!h->mlp_ready) { h->err = "no MLP parameters"; return FP_ERR_STATE; }
+  CK(cudaMemcpyAsync(h->xb, x, (size_t)rows * MLP_NIN * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->yb, y, rows * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->loss_acc, 0, sizeof(double), h->stream));
+  TRY(mlp_loss_grad(h, h->xb, h->yb, rows));
+  CK(cudaMemcpyAsync(grad, h->mlpG, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  double l = 0;
+  CK(cudaMemcpyAsync(&l, h->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (loss) *loss = l;
+  return FP_OK;
+}
+
+// Adam on minibatches of the recorded samples; the order of the samples in every epoch is a
+// Fisher-Yates shuffle driven by SplitMix64 (seed, epoch).
+fp_status fp_learned_train(fp_handle *h, int epochs, int batch, double lr, unsigned long long seed, double *last_loss) {
+  if (!h || epochs < 1 || batch < 32 || batch > fp_handle::CH || !(lr > 0)) return FP_ERR_INVALID;
+  if (h->n_samples < batch) { h->err = "fp_learned_train: fewer recorded samples than one batch"; return FP_ERR_STATE; }
+  TRY(mlp_ensure_init(h, seed));
+  const long long ns = h->n_samples;
+  const long long nb = ns / batch;
+  std::vector<int> perm(ns);
+  int *didx = nullptr;
+  TRY(dalloc(h, &didx, (size_t)ns));
+  double epoch_loss = 0;
+  for (int e = 0; e < epochs; ++e) {
+    for (long long i = 0; i < ns; ++i) perm[i] = (int)i;
+    unsigned long long ctr = 0;
+    for (long long i = ns - 1; i > 0; --i) {
+      unsigned long long z = (seed ^ (0x5851F42D4C957F2DULL * (e + 1))) + (++ctr) * 0x9E3779B97F4A7C15ULL;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+      z ^= z >> 31;
+      std::swap(perm[i], perm[z % (unsigned long long)(i + 1)]);
+    }
+    CK(cudaMemcpyAsync(didx, perm.data(), ns * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->loss_acc, 0, sizeof(double), h->stream));
+    for (long long b = 0; b < nb; ++b) {
+      k_gather_rows<<<(batch * (MLP_NIN + 1) + 255) / 256, 256, 0, h->stream>>>(batch, didx + b * batch, h->SX, h->SY,
+                                                                                h->xb, h->yb);
+      CKL();
+      TRY(mlp_loss_grad(h, h->xb, h->yb, batch));
+      k_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, h->stream>>>(h->mlpP, h->mlpG, h->mlpM1, h->mlpM2, MLP_NPARAM,
+                                                              (float)lr, 0.9f, 0.999f, 1e-8f, ++h->adam_step);
+      CKL();
+    }
+    double l = 0;
+    CK(cudaMemcpyAsync(&l, h->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    epoch_loss = l / nb;
+  }
+  if (last_loss) *last_loss = epoch_loss;
   return FP_OK;
 }
 

@@ -31,7 +31,10 @@ EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_ge
             "fp_apply_precond", "fp_apply_projection", "fp_apply_projection_noalloc",
             "fp_get_dof_map",
             "fp_get_local_matrix", "fp_get_step_timing", "fp_set_option", "fp_set_profiling",
-            "fp_get_kernel_stats", "fp_last_error", "fp_destroy"]
+            "fp_get_kernel_stats", "fp_learned_record", "fp_learned_use", "fp_learned_train",
+            "fp_learned_num_samples", "fp_mlp_init", "fp_mlp_set_params", "fp_mlp_get_params",
+            "fp_mlp_forward", "fp_mlp_loss_grad", "fp_last_error", "fp_destroy"]
+MLP_NPARAM = 8 * 256 + 256 + 256 * 256 + 256 + 256 + 1
 
 
 class MeshDesc(ctypes.Structure):
@@ -64,7 +67,9 @@ class KernelStats(ctypes.Structure):
 
 class StepStats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("iterations", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
+                ("lambda0_learned", ctypes.c_int), ("guess_res_prev", ctypes.c_double),
+                ("guess_res_learned", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -86,6 +91,16 @@ _lib.fp_get_step_timing.argtypes = [_vp, _vp]
 _lib.fp_set_option.argtypes = [_vp, ctypes.c_char_p, ctypes.c_double]
 _lib.fp_set_profiling.argtypes = [_vp, ctypes.c_int]
 _lib.fp_get_kernel_stats.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(KernelStats)]
+_lib.fp_learned_record.argtypes = [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]
+_lib.fp_learned_use.argtypes = [_vp, ctypes.c_int]
+_lib.fp_learned_train.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong,
+                                  ctypes.POINTER(ctypes.c_double)]
+_lib.fp_learned_num_samples.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+_lib.fp_mlp_init.argtypes = [_vp, ctypes.c_ulonglong]
+_lib.fp_mlp_set_params.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.fp_mlp_get_params.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.fp_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int, _vp]
+_lib.fp_mlp_loss_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]
 _lib.fp_last_error.argtypes = [_vp]
 _lib.fp_last_error.restype = ctypes.c_char_p
 _lib.fp_destroy.argtypes = [_vp]
@@ -165,7 +180,9 @@ class Solver:
         if not allow_failure:
             self._check(rc)
         return {"status": rc, "step": st.step, "iterations": st.iterations,
-                "rel_residual": st.rel_residual, "true_rel_residual": st.true_rel_residual}
+                "rel_residual": st.rel_residual, "true_rel_residual": st.true_rel_residual,
+                "lambda0_learned": st.lambda0_learned, "guess_res_prev": st.guess_res_prev,
+                "guess_res_learned": st.guess_res_learned}
 
     def run(self, n_steps):
         st = StepStats()
@@ -214,6 +231,50 @@ class Solver:
         """v, out: CUDA tensors (float64, n_lambda) on the handle's device."""
         self._check(_lib.fp_apply_projection_noalloc(self._h, v.data_ptr(), out.data_ptr()))
         return out
+
+    # learned initial guess -----------------------------------------------------
+    def learned_record(self, on=True, max_samples=4_000_000, per_step=65536):
+        self._check(_lib.fp_learned_record(self._h, 1 if on else 0, int(max_samples), int(per_step)))
+
+    def learned_use(self, on=True):
+        self._check(_lib.fp_learned_use(self._h, 1 if on else 0))
+
+    def learned_train(self, epochs, batch=8192, lr=1e-3, seed=0):
+        loss = ctypes.c_double()
+        self._check(_lib.fp_learned_train(self._h, epochs, batch, lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+    def learned_num_samples(self):
+        n = ctypes.c_longlong()
+        self._check(_lib.fp_learned_num_samples(self._h, ctypes.byref(n)))
+        return n.value
+
+    def mlp_init(self, seed):
+        self._check(_lib.fp_mlp_init(self._h, seed))
+
+    def mlp_set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        self._check(_lib.fp_mlp_set_params(self._h, t.ctypes.data, t.size))
+
+    def mlp_get_params(self):
+        t = np.empty(MLP_NPARAM, dtype=np.float32)
+        self._check(_lib.fp_mlp_get_params(self._h, t.ctypes.data, t.size))
+        return t
+
+    def mlp_forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty(x.shape[0], dtype=np.float32)
+        self._check(_lib.fp_mlp_forward(self._h, x.ctypes.data, x.shape[0], out.ctypes.data))
+        return out
+
+    def mlp_loss_grad(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        g = np.empty(MLP_NPARAM, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(_lib.fp_mlp_loss_grad(self._h, x.ctypes.data, y.ctypes.data, x.shape[0], g.ctypes.data,
+                                          ctypes.byref(loss)))
+        return loss.value, g
 
     def get_dof_map(self, s):
         n = ctypes.c_int()

@@ -1,0 +1,112 @@
+"""Learned initial guess: the library's MLP kernels against the CPU oracle (oracle/mlp.py),
+and the gain of the trained network over the previous-step guess on unseen steps."""
+import numpy as np
+import pytest
+
+from paper_2509_06673_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_06673_gb300 import build
+    build.build()
+    from paper_2509_06673_gb300 import fetipe
+    return fetipe
+
+
+@pytest.fixture(scope="module")
+def solver(F):
+    sol = F.Solver(W.small_case(2, 2, 3, k=2, lame_lambda=9.0, tau=1e-2))
+    yield sol
+    sol.close()
+
+
+def test_init_matches_oracle(solver):
+    from oracle import mlp
+    solver.mlp_init(12345)
+    got = solver.mlp_get_params()
+    ref = mlp.init_params(12345).astype(np.float32)
+    assert np.array_equal(got, ref)
+
+
+def test_forward_and_gradient_match_oracle(solver):
+    """GPU forward and gradient (tensor cores: bfloat16 operands, FP32 accumulation) against
+    the FP64 oracle that rounds the same operands to bfloat16."""
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    theta = (mlp.init_params(7) * 0.5)
+    p = mlp.unpack(theta)
+    p["W3"] = np.random.default_rng(8).uniform(-0.1, 0.1, size=256)
+    p["b3"] = np.array([0.1])
+    theta = mlp.pack(p).astype(np.float32).astype(np.float64)
+    solver.mlp_set_params(theta)
+    m = 1000                      # not a multiple of the 64-row tile
+    x = rng.normal(size=(m, mlp.NIN)).astype(np.float32).astype(np.float64)
+    y = rng.normal(size=m).astype(np.float32).astype(np.float64)
+    out_ref, _ = mlp.forward(theta, x, bf16_points=True)
+    out = solver.mlp_forward(x)
+    assert np.abs(out - out_ref).max() <= 2e-5 * np.abs(out_ref).max()
+    L_ref, g_ref = mlp.loss_grad(theta, x, y, bf16_points=True)
+    L, g = solver.mlp_loss_grad(x, y)
+    assert abs(L - L_ref) <= 1e-5 * L_ref
+    p_ref, p_got = mlp.unpack(g_ref), mlp.unpack(g.astype(np.float64))
+    for name, _ in mlp.SIZES:
+        a, b = p_got[name], p_ref[name]
+        assert np.linalg.norm(a - b) <= 2e-4 * np.linalg.norm(b), name
+    # the bfloat16 operand rounding is visible against the unrounded FP64 network
+    _, g64 = mlp.loss_grad(theta, x, y, bf16_points=False)
+    assert np.linalg.norm(g - g64) > 10 * np.linalg.norm(g - g_ref)
+
+
+def _point_case(seed_node, n_steps):
+    c = W.small_case(6, 6, 6, k=2, lame_lambda=9.0, tau=2e-3, n_steps=n_steps, tol=1e-8, source="point",
+                     q_omega=25.0)
+    return c.with_(src_node=W.point_source_node(c, seed_node))
+
+
+def test_learned_guess_reduces_iterations(F):
+    """Train on the steps of one source location, evaluate on another (unseen) location at
+    the metric's tolerance 1e-8: the learned guess starts PCG from a much smaller true
+    residual than lambda^{n-1} and saves iterations; the judge keeps the solution exact."""
+    train = F.Solver(_point_case(1000, 80))
+    train.assemble()
+    train.factor()
+    train.learned_record(True, max_samples=2_000_000)
+    for _ in range(80):
+        train.step()
+    assert train.learned_num_samples() > 10000
+    loss = train.learned_train(epochs=40, batch=4096, lr=2e-3, seed=1)
+    assert np.isfinite(loss)
+    theta = train.mlp_get_params()
+    train.close()
+
+    def run(learned):
+        sol = F.Solver(_point_case(1001, 60))
+        sol.assemble()
+        sol.factor()
+        if learned:
+            sol.mlp_set_params(theta)
+            sol.learned_use(True)
+        its, wins, ratio = [], 0, []
+        for _ in range(60):
+            st = sol.step()
+            assert st["true_rel_residual"] <= 1e-8
+            its.append(st["iterations"])
+            wins += st["lambda0_learned"]
+            if learned and st["guess_res_prev"] > 0:
+                ratio.append(st["guess_res_learned"] / st["guess_res_prev"])
+        lam = sol.get_lambda()
+        sol.close()
+        return np.array(its), wins, lam, np.array(ratio)
+
+    its0, _, lam0, _ = run(False)
+    its1, wins, lam1, ratio = run(True)
+    assert np.abs(lam1 - lam0).max() <= 1e-6 * np.abs(lam0).max()   # same solution (tol 1e-8)
+    assert wins >= 40                                                 # the network wins the judge
+    assert np.median(ratio) < 0.1                                     # 10x smaller starting residual
+    assert its1[5:].sum() < 0.9 * its0[5:].sum(), (its0, its1)
