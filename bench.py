@@ -174,7 +174,8 @@ def run_native(args):
     case = workload(args.config, args.precision)
     stream = torch.cuda.current_stream()
     sol = F.Solver(case, stream=stream.cuda_stream)
-    for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk)):
+    for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
+                     ("factor_fp64", args.factor_fp64)):
         if val is not None:
             sol.set_option(key, val)
     t0 = time.perf_counter()
@@ -308,6 +309,7 @@ def main():
     ap.add_argument("--solve-kernel", type=int, default=None, help="1 blocked sweeps, 0 row-step sweeps")
     ap.add_argument("--wpc", type=int, default=None, help="warps per CTA of the local solves")
     ap.add_argument("--chunk", type=int, default=None, help="bytes per shared-memory stage of the solves")
+    ap.add_argument("--factor-fp64", type=int, default=None, help="mixed: factor in FP64, round to FP32")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

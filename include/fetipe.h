@@ -240,7 +240,10 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *   "solve_kernel" [1]  local solve kernel: 1 blocked sweeps (32-row blocks, inverse diagonal
  *                       blocks), 0 row-step sweeps
  *   "solve_wpc"    [0]  warps per CTA of the local solves, 1..8 (0: chosen from the task count)
- *   "solve_chunk"  [8192] bytes per shared-memory stage of the blocked solves, 4096..65536 */
+ *   "solve_chunk"  [8192] bytes per shared-memory stage of the blocked solves, 4096..65536
+ *   "factor_fp64"  [1]  mixed precision: compute the local factors in FP64 (temporary device
+ *                       memory) and round the finished factors to FP32 (0: factor in FP32);
+ *                       takes effect at the next fp_factor */
 fp_status fp_set_option(fp_handle *h, const char *key, double value);
 
 /* Per-kernel-class timing (CUDA events on the handle's stream around every launch of the

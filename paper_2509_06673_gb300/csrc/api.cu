@@ -26,6 +26,7 @@ cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int ch
                                   int *counter, int *status, const int *done);
 cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
                              cudaStream_t stream);
+cudaError_t launch_round_to_float(const double *src, float *dst, long long n, cudaStream_t stream);
 __global__ void k_dot(const double *, const double *, long long, double *, unsigned *, double *, int *, int,
                       double *, int);
 __global__ void k_pcg_update(double *, double *, const double *, const double *, long long, double *, unsigned *,
@@ -99,6 +100,7 @@ struct fp_handle {
   int solve_kernel = 1;    // 1: blocked sweeps with inverse diagonal blocks, 0: row-step sweeps
   int solve_wpc = 0;       // warps per CTA of the solve kernels (0: automatic)
   int solve_chunk = 8192;  // bytes per ring stage of the blocked solve
+  int factor_fp64 = 1;     // mixed precision: factor in FP64, round the finished factor to FP32
   double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
   BandTask *tasksN = nullptr, *tasksD = nullptr, *taskH = nullptr, *tasksHinv = nullptr;
   int ntask = 0, mmax = 4, mmaxH = 4, ldmax = 32;
@@ -633,6 +635,33 @@ fp_status factor_T(fp_handle *h) {
   }
   fN = (T *)h->facN; fD = (T *)h->facD;
   const bool f32 = sizeof(T) == 4;
+  if (f32 && h->factor_fp64) {
+    // FP64 factorisation in temporary arrays, then one rounding of the finished factor (and of
+    // its inverse diagonal blocks, computed in FP64 from the FP64 factor) to FP32
+    double *tN = nullptr, *tL = nullptr;
+    CK(cudaMalloc(&tN, nf * sizeof(double)));
+    cudaError_t e = cudaMalloc(&tL, (size_t)h->linv_total * sizeof(double));
+    if (e != cudaSuccess) { cudaFree(tN); h->err = cudaGetErrorString(e); return FP_ERR_OOM; }
+    int NB = 32;
+    while (NB > 4 && (size_t)NB * (h->ldmax + 1) * sizeof(double) > 200 * 1024) NB /= 2;
+    const size_t smem = (size_t)NB * (h->ldmax + 1) * sizeof(double);
+    fp_status st = FP_OK;
+    for (int mode = 0; mode < 2 && st == FP_OK; ++mode) {
+      T *dstF = (T *)(mode == 0 ? h->facN : h->facD);
+      T *dstL = (T *)(mode == 0 ? h->linvN : h->linvD);
+      const BandTask *tk = mode == 0 ? h->tasksN : h->tasksD;
+      cudaError_t ee = launch_csr_to_band(false, h->D, h->csr_val, tN, mode, h->stream);
+      if (ee == cudaSuccess) ee = launch_band_factor(false, tk, h->ntask, tN, NB, h->status, smem, h->stream);
+      if (ee == cudaSuccess) ee = launch_band_linv(false, tk, h->ntask, tN, tL, h->stream);
+      if (ee == cudaSuccess) ee = launch_round_to_float(tN, (float *)dstF, (long long)nf, h->stream);
+      if (ee == cudaSuccess) ee = launch_round_to_float(tL, (float *)dstL, h->linv_total, h->stream);
+      if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaFree(tN);
+    cudaFree(tL);
+    return st;
+  }
   CK(launch_csr_to_band(f32, h->D, h->csr_val, fN, 0, h->stream));
   CK(launch_csr_to_band(f32, h->D, h->csr_val, fD, 1, h->stream));
   int NB = 32;
@@ -1193,6 +1222,7 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "pcg_chunk") { if (v < 1 || v > 256) return bad(); h->pcg_chunk = v; }
   else if (k == "solve_kernel") { if (v < 0 || v > 1) return bad(); h->solve_kernel = v; }
   else if (k == "solve_wpc") { if (v < 0 || v > 8) return bad(); h->solve_wpc = v; }
+  else if (k == "factor_fp64") { if (v < 0 || v > 1) return bad(); h->factor_fp64 = v; }
   else if (k == "solve_chunk") { if (v < 4096 || v > 65536 || v % 1024) return bad(); h->solve_chunk = v; }
   else { h->err = "fp_set_option: unknown key " + k; return FP_ERR_INVALID; }
   return FP_OK;

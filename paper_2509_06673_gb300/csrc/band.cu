@@ -685,6 +685,16 @@ cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int ch
                                     (const double *)linv, x, counter, status, done);
 }
 
+__global__ void k_round_to_float(const double *src, float *dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+cudaError_t launch_round_to_float(const double *src, float *dst, long long n, cudaStream_t stream) {
+  k_round_to_float<<<2048, 256, 0, stream>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
                              cudaStream_t stream) {
   if (fp32) k_band_linv<float><<<ntask, 256, 0, stream>>>(tasks, ntask, (const float *)fac, (float *)linv);
