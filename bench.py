@@ -107,6 +107,25 @@ def peaks():
 
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate of the profiling recipe's table
 
+# DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch, profiles/k_band_solve_float_config5_launches.md).  The
+# record holds only while the kernel source and its launch shape are the ones captured.
+TRAFFIC_RECORDS = [
+    {"workload": "config5", "precision": "mixed", "kernel": "k_band_solve_blk<float>",
+     "shape": None, "band_cu_sha256": None, "bytes_per_launch": None},
+]
+
+
+def traffic_of(workload, precision, shape):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2509_06673_gb300", "csrc", "band.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for r in TRAFFIC_RECORDS:
+        if (r["workload"] == workload and r["precision"] == precision and r["band_cu_sha256"] == digest
+                and r["shape"] == shape and r["bytes_per_launch"]):
+            return r["bytes_per_launch"]
+    return None
+
 
 def cpu_baseline(case, n_steps=1):
     """Oracle FETI on the bounded sample; returns (steps/s scaled to the full workload, info)."""
@@ -175,15 +194,33 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     sol = F.Solver(case, stream=stream.cuda_stream)
     for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
-                     ("factor_fp64", args.factor_fp64)):
+                     ("factor_fp64", args.factor_fp64), ("graph", args.graph)):
         if val is not None:
             sol.set_option(key, val)
     t0 = time.perf_counter()
     sol.assemble()
     sol.factor()
     setup_s = time.perf_counter() - t0
+    tuning = sol.tuning()
+    learned = bool(args.learned) and case.precision == "mixed"
+    train_s, train_loss, record_s = None, None, None
+    if learned:
+        # setup of the learned lambda_0 (outside the timed region): the solver records
+        # (features, lambda increment) samples over its first steps, then the network is
+        # trained on them with the library's own kernels
+        t0 = time.perf_counter()
+        sol.learned_record(True, max_samples=4_000_000)
+        for _ in range(args.learned_record_steps):
+            sol.step()
+        record_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        train_loss = sol.learned_train(epochs=args.learned_epochs, batch=4096, lr=2e-3, seed=1)
+        train_s = time.perf_counter() - t0
+        sol.learned_record(False)
+        sol.learned_use(True)
     for _ in range(args.warmup):
         sol.step()
+    warmup = args.warmup
 
     def barrier():
         if world > 1:
@@ -196,10 +233,15 @@ def run_native(args):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    its, restarts = [], []
+    torch.cuda.nvtx.range_push("timed_region")  # lets ncu select the timed launches
+    its, restarts, wins, stags = [], [], [], []
     for _ in range(args.steps):
-        its.append(sol.step()["iterations"])
-        restarts.append(int(sol.step_timing()[3]))
+        st = sol.step()
+        its.append(st["iterations"])
+        wins.append(st["lambda0_learned"])
+        restarts.append(st["restarts"])
+        stags.append(st["stagnations"])
+    torch.cuda.nvtx.range_pop()
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -244,10 +286,18 @@ def run_native(args):
         ach = kN["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": None, "kernel": "k_band_solve_blk<float>" if args.solve_kernel != 0 else "k_band_solve<float>", "peak_source": src + " (burst copy)"}
-    roof.update({"launches": launches, "avg_launch_ms": avg_ms,
-                 "share_of_step": (kN["total_ms"] + kD["total_ms"]) / ms})
+    shape = [tuning["solve_wpc"], tuning["solve_chunk"], tuning["solve_ctas_per_sm"]]
+    roof["traffic"] = traffic_of(args.config, case.precision, shape)
+    roof.update({"launch_shape": {"warps_per_cta": shape[0], "stage_bytes": shape[1], "ctas_per_sm": shape[2]},
+                 "algorithmic_bytes_per_launch": kN["bytes_per_launch"],
+                 "launches_timed": launches, "avg_launch_ms": avg_ms,
+                 "timed_launches": "CUDA events around every local solve outside the device-side "
+                                   "PCG loop (a conditional graph body holds no events): the "
+                                   "right-hand side, reference, initial and learned-guess solves "
+                                   "with their refinement sweeps" if args.graph != 0 else
+                                   "CUDA events around every local solve launch"})
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "warmup": warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if case.precision == "fp64" else "f32 local / f64 outer",
             "data": "synthetic",
@@ -255,6 +305,13 @@ def run_native(args):
                        "subdomains": case.nsub, "n_lambda": s.n_lambda, "dofs": s.n_dofs,
                        "factor_gb": s.factor_bytes / 1e9, "l2": "inputs larger than L2 (factors %.1f GB)"
                        % (s.factor_bytes / 1e9), "setup_s": setup_s, "pcg_iterations": its, "pcg_restarts": restarts,
+                       "pcg_stagnation_stops": stags, "autotuned": tuning,
+                       "graph": args.graph != 0, "learned_lambda0": learned,
+                       "learned_guess_chosen": wins if learned else None,
+                       "learned_record_steps": args.learned_record_steps if learned else 0,
+                       "learned_record_s": record_s, "learned_train_s": train_s,
+                       "learned_train_loss": train_loss,
+                       "first_timed_step": (args.learned_record_steps if learned else 0) + args.warmup + 1,
                        "parallelism": "replicas (one independent problem per GPU)"},
             "roofline": roof, "clocks": clk,
             "e2e": {"value": world * args.steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 0,
@@ -310,6 +367,11 @@ def main():
     ap.add_argument("--wpc", type=int, default=None, help="warps per CTA of the local solves")
     ap.add_argument("--chunk", type=int, default=None, help="bytes per shared-memory stage of the solves")
     ap.add_argument("--factor-fp64", type=int, default=None, help="mixed: factor in FP64, round to FP32")
+    ap.add_argument("--graph", type=int, default=None, help="1: one CUDA graph launch per time step")
+    ap.add_argument("--learned", type=int, default=1, help="mixed arm: learned lambda_0 (trained in warm-up)")
+    ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--learned-record-steps", type=int, default=10,
+                    help="steps the solver records for training the lambda_0 network (setup)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -115,6 +115,8 @@ typedef struct {
   int lambda0_learned;       /* 1 if the learned initial guess won the judge this step */
   double guess_res_prev;     /* relative true residual of the lambda^{n-1} guess (-1: not computed) */
   double guess_res_learned;  /* relative true residual of the learned guess (-1: not computed) */
+  int restarts;              /* restarts of Algorithm 1 from the true residual */
+  int stagnations;           /* rounds stopped because the recursive residual stalled */
 } fp_step_stats;
 
 /* Copies the mesh description and parameters, builds the dof numbering, band ordering and
@@ -233,17 +235,42 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  * out of range.
  *   "ir_sweeps"    [6]  maximum FP64 refinement sweeps of the accurate local solves (mixed
  *                       precision: d = B K^+ f, the true residual, the recovery), 0..16
- *   "ir_eps"       [1e-13] refinement stops once ||dx||_2 <= ir_eps ||x||_2 (all subdomains)
+ *   "ir_eps"       [1e-12] refinement stops once ||dx||_2 <= ir_eps ||x||_2 (all subdomains)
+ *   "ir_stag"      [0.5] ... or once ||dx||_2 > ir_stag ||dx_prev||_2 (stagnation at the
+ *                       rounding floor), 0 <= ir_stag < 1, 0 never
  *   "inner_ir"     [0]  refinement sweeps of the local solves inside the PCG loop, 0..8
  *   "max_restarts" [8]  restarts of PCG from the true residual, 0..64
- *   "pcg_chunk"    [8]  PCG iterations launched between two host polls of the stop flag, 1..256
+ *   "pcg_chunk"    [8]  PCG iterations per body of the device-side loop (per host poll of the
+ *                       stop flag when "graph" is 0), 1..256
  *   "solve_kernel" [1]  local solve kernel: 1 blocked sweeps (32-row blocks, inverse diagonal
  *                       blocks), 0 row-step sweeps
- *   "solve_wpc"    [0]  warps per CTA of the local solves, 1..8 (0: chosen from the task count)
- *   "solve_chunk"  [8192] bytes per shared-memory stage of the blocked solves, 4096..65536
+ *   "solve_wpc"    [0]  warps per CTA of the local solves, 1..8 (0: autotuned, or chosen
+ *                       from the task count when "autotune" is 0)
+ *   "solve_chunk"  [0]  bytes per shared-memory stage of the blocked solves, 4096..65536
+ *                       (0: autotuned, or 8192)
+ *   "solve_cps"    [0]  CTAs per SM of the blocked solves, 1..2 (0: autotuned, or 1)
+ *   "factor_nb"    [0]  panel width of the factorisation, 4..64, multiple of 4 (0: autotuned,
+ *                       or the widest of 32, 16, 8, 4 whose panel fits in shared memory)
+ *   "autotune"     [1]  fp_factor times candidate launch shapes on the handle's own factors
+ *                       and keeps the fastest (see fp_get_tuning); explicitly set shape
+ *                       options are kept fixed.  Takes effect at the next fp_factor.
  *   "factor_fp64"  [1]  mixed precision: compute the local factors in FP64 (temporary device
  *                       memory) and round the finished factors to FP32 (0: factor in FP32);
- *                       takes effect at the next fp_factor */
+ *                       takes effect at the next fp_factor
+ *   "graph"        [1]  1: fp_step is one CUDA graph launch: the step is captured once (on
+ *                       private streams; re-captured after an option, fp_factor,
+ *                       fp_set_profiling or the learned-guess mode changes) with Algorithm 1
+ *                       and its restarts as conditional WHILE nodes set by device flags, and
+ *                       replayed on the handle's stream; 0: the same kernels launched
+ *                       directly, with a host poll every pcg_chunk iterations.  Both give
+ *                       bit-identical results.
+ *   "stag_window"  [60] a round of Algorithm 1 stops (and restarts from the true residual)
+ *                       when its recursive residual has not halved within this many
+ *                       iterations; 0 never, 1..100000
+ *   "judge"        [0]  how the learned lambda_0 is judged against the previous-step guess:
+ *                       0 the 2-norm of the projected residual P r, 1 the preconditioned
+ *                       residual (P r, P M^-1 P r), an estimate of the error in the F-norm
+ *                       (two more preconditioner applications per step) */
 fp_status fp_set_option(fp_handle *h, const char *key, double value);
 
 /* Per-kernel-class timing (CUDA events on the handle's stream around every launch of the
@@ -260,6 +287,20 @@ typedef struct {
 } fp_kernel_stats;
 fp_status fp_set_profiling(fp_handle *h, int on);
 fp_status fp_get_kernel_stats(const fp_handle *h, int kind, fp_kernel_stats *out);
+
+/* Launch shapes chosen by the autotuner at the last fp_factor (FP_ERR_STATE before it).
+ * factor_nb: panel width, timed on a factorisation of the 2 x (SM count) largest subdomains
+ * after a fresh copy of their band (factor_ms: that time for the chosen width); solve_*:
+ * warps per CTA, bytes per shared-memory stage and CTAs per SM of the blocked solves, timed
+ * on whole Neumann solves (solve_ms: one solve with the chosen shape; candidates: shapes
+ * timed).  With "autotune" 0 the fields hold the shapes in use and the timings are 0. */
+typedef struct {
+  int factor_nb;
+  int solve_wpc, solve_chunk, solve_ctas_per_sm;
+  double factor_ms, solve_ms;
+  int candidates;
+} fp_tuning;
+fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out);
 
 const char *fp_last_error(const fp_handle *h);
 void fp_destroy(fp_handle *h);

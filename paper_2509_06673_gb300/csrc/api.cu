@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "device.cuh"
@@ -41,15 +42,22 @@ __global__ void k_bnd_apply(DevTopo, const double *, const double *, double *, c
 __global__ void k_Gt(DevTopo, const double *, double *, const int *);
 __global__ void k_gemv(const double *, const double *, double *, int, const int *);
 __global__ void k_Gcomb(DevTopo, const double *, const double *, double, double *, const int *);
-__global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, const double *, double,
-                      double *, double *);
+__global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, const double *,
+                      const double *, double *, double *);
+__global__ void k_loop_arm_outer(cudaGraphConditionalHandle, int *);
+__global__ void k_loop_arm_inner(cudaGraphConditionalHandle, int *);
+__global__ void k_loop_inner(cudaGraphConditionalHandle, int *, int);
+__global__ void k_loop_outer(cudaGraphConditionalHandle, int *, const double *, int);
+__global__ void k_copy_if(double *, const double *, long long, const int *);
 __global__ void k_recover(DevTopo, DevParams, const double *, const double *, const double *, double *, double *,
                           double *, double *, double *);
 cudaError_t launch_band_to_dense(const double *band, int n, int LD, int b, double *out, cudaStream_t s);
 __global__ void k_identity(double *, int);
 __global__ void k_residual_N(DevTopo, const double *, const double *, const double *, double *, const int *);
+__global__ void k_csr_to_sell(DevTopo, const double *, double *);
 __global__ void k_local_add(double *, const double *, long long, const int *);
-__global__ void k_ir_check(const double *, const double *, long long, double, double *, unsigned *, int *);
+__global__ void k_ir_check(const double *, const double *, long long, double, double *, unsigned *, int *,
+                           double *, double);
 
 // learned lambda_0 (learned.cu)
 constexpr int MLP_NIN = 8, MLP_NH = 256, MLP_NPARAM = 8 * 256 + 256 + 256 * 256 + 256 + 256 + 1;
@@ -66,8 +74,8 @@ __global__ void k_mlp_dw1(int, const float *, const float *, float *);
 __global__ void k_sum_double(const double *, int, double *);
 __global__ void k_adam(float *, const float *, float *, float *, int, float, float, float, float, int);
 __global__ void k_mlp_init(float *, unsigned long long);
-__global__ void k_features(int, const double *, const double *, const double *, double, const float *, const int *,
-                           const int *, float *, float *);
+__global__ void k_features(int, const double *, const double *, const double *, const double *, const float *,
+                           const int *, const int *, float *, float *);
 __global__ void k_guess(int, const double *, const float *, const float *, const double *, double *);
 __global__ void k_record(int, const float *, const double *, const double *, const double *, int, int, long long,
                          long long, float *, float *);
@@ -94,12 +102,19 @@ struct fp_handle {
   DevParams DP{};
   // matrices
   double *csr_val = nullptr, *fstat = nullptr, *Zn = nullptr, *E0n = nullptr, *Reta = nullptr;
+  double *sell_val = nullptr;  // sliced ELL copy of the Neumann matrices (FP64 residuals)
   void *facN = nullptr, *facD = nullptr, *linvN = nullptr, *linvD = nullptr;
   double *linvH = nullptr;
   long long linv_total = 0;
   int solve_kernel = 1;    // 1: blocked sweeps with inverse diagonal blocks, 0: row-step sweeps
-  int solve_wpc = 0;       // warps per CTA of the solve kernels (0: automatic)
-  int solve_chunk = 8192;  // bytes per ring stage of the blocked solve
+  int solve_wpc = 0;       // warps per CTA of the solve kernels (0: autotuned / from the task count)
+  int solve_chunk = 0;     // bytes per ring stage of the blocked solve (0: autotuned / 8192)
+  int solve_cps = 0;       // CTAs per SM of the blocked solve (0: autotuned / 1)
+  int factor_nb = 0;       // panel width of the factorisation (0: autotuned / widest that fits)
+  int autotune = 1;        // time candidate shapes at fp_factor and keep the fastest
+  struct SolveShape { int wpc, chunk, cps; };
+  SolveShape shape{0, 0, 0};  // launch shape of the blocked solves (set at fp_factor)
+  fp_tuning tuning{};
   int factor_fp64 = 1;     // mixed precision: factor in FP64, round the finished factor to FP32
   double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
   BandTask *tasksN = nullptr, *tasksD = nullptr, *taskH = nullptr, *tasksHinv = nullptr;
@@ -110,15 +125,30 @@ struct fp_handle {
   double *XF = nullptr, *XA = nullptr, *XR = nullptr;  // rhs, refined solution, residual
   // tunables (fp_set_option)
   int ir_sweeps = 6;       // max refinement sweeps of the accurate local solves (mixed precision)
-  double ir_eps = 1e-13;   // refinement stops once ||dx|| <= ir_eps ||x||
+  double ir_eps = 1e-12;   // refinement stops once ||dx|| <= ir_eps ||x||
+  double ir_stag = 0.5;    // ... or once ||dx|| > ir_stag ||dx_prev|| (0: never)
   int inner_ir = 0;        // refinement sweeps inside the PCG loop (mixed precision)
   int max_restarts = 8;    // PCG restarts from the true residual
-  int pcg_chunk = 8;       // PCG iterations launched between host polls
+  int pcg_chunk = 8;       // PCG iterations per body of the device loop (per host poll without graphs)
+  int use_graph = 1;       // 1: each time step is one CUDA graph launch (device-side loops)
+  int stag_window = 60;    // PCG round stops after this many iterations without halving
+  int judge = 0;           // learned guess judged by 0: ||P r||_2, 1: (P r, P M^-1 P r)
   int restarts_last = 0;
+  // per-step graph: captured on private streams, launched on `stream`
+  cudaStream_t cap[3] = {};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int gkey = -1;             // learned-guess variant the graph was captured with
+  int gdirty = 1;            // options, profiling or factors changed since the capture
+  int capturing = 0, in_body = 0;
+  std::vector<cudaEvent_t> gev;  // events recorded by the graph (profiling)
+  size_t gev_used = 0;
+  double *stepv = nullptr, *h_stepv = nullptr;  // per-step scalars (device, pinned host)
+  int *h_flinit = nullptr;                      // initial PCG flags (pinned host)
   double *lam = nullptr, *lam_prev = nullptr, *lam00 = nullptr, *d = nullptr, *r = nullptr, *z = nullptr,
          *p = nullptr, *q = nullptr, *t1 = nullptr, *t2 = nullptr;
   double *ce = nullptr, *cy = nullptr, *calpha = nullptr;
-  double *partial = nullptr, *sc = nullptr;
+  double *partial = nullptr, *sc = nullptr, *ir_prev = nullptr;
   unsigned *red_counter = nullptr;
   int *fl = nullptr, *fl_zero = nullptr, *fl_ir = nullptr, *h_fl = nullptr;
   double *h_sc = nullptr;
@@ -130,7 +160,9 @@ struct fp_handle {
   int profiling = 0;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  std::vector<std::pair<int, size_t>> pending;  // (kind, index of the start event)
+  struct Pending { int kind; cudaEvent_t e0, e1; };
+  std::vector<Pending> pending;   // timed launches of the current step
+  std::vector<Pending> gpending;  // timed launches inside the captured graph
   long long prof_launches[2] = {0, 0};
   double prof_ms[2] = {0, 0};
   double bytes_per_solve = 0, flops_per_solve = 0;
@@ -225,6 +257,8 @@ fp_status build_device(fp_handle *h) {
     d.is_bnd = put(isb);
     d.halo_ptr = put(t.halo_ptr); d.halo_row = put(t.halo_row); d.halo_ent = put(t.halo_ent);
     d.elem_dofs = put(t.elem_dofs);
+    d.sell_ptr = put(t.sell_ptr); d.sell_col = put(t.sell_col); d.sell_src = put(t.sell_src);
+    d.nslice = (int)t.sell_ptr.size() - 1;
     tpls.push_back(d);
     h->nbnd_max = std::max(h->nbnd_max, d.nbnd);
     h->ldmax = std::max(h->ldmax, t.LD);
@@ -238,7 +272,7 @@ fp_status build_device(fp_handle *h) {
   TRY(upload(h, &D.sub_x0, T.sub_x0)); TRY(upload(h, &D.sub_y0, T.sub_y0));
   TRY(upload(h, &D.sub_hx, T.sub_hx)); TRY(upload(h, &D.sub_hy, T.sub_hy));
   TRY(upload(h, &D.vec_off, T.vec_off)); TRY(upload(h, &D.fac_off, T.fac_off));
-  TRY(upload(h, &D.csr_off, T.csr_off)); TRY(upload(h, &D.unode_off, T.unode_off));
+  TRY(upload(h, &D.csr_off, T.csr_off)); TRY(upload(h, &D.sell_off, T.sell_off)); TRY(upload(h, &D.unode_off, T.unode_off));
   TRY(upload(h, &D.pnode_off, T.pnode_off)); TRY(upload(h, &D.elem_off, T.elem_off));
   TRY(upload(h, &D.bsc_off, T.bsc_off));
   TRY(upload(h, &D.sub_I0, T.sub_I0)); TRY(upload(h, &D.sub_J0, T.sub_J0));
@@ -308,6 +342,7 @@ fp_status build_device(fp_handle *h) {
   // ---- work arrays ----
   const long long nv = T.vec_off[T.S], nl = std::max(T.n_lambda, 1);
   TRY(dalloc(h, &h->csr_val, (size_t)T.csr_off[T.S]));
+  if (h->P.precision == FP_PREC_MIXED) TRY(dalloc(h, &h->sell_val, (size_t)T.sell_off[T.S]));
   TRY(dalloc(h, &h->fstat, (size_t)nv));
   TRY(dalloc(h, &h->Zn, (size_t)T.pnode_off[T.S]));
   TRY(dalloc(h, &h->E0n, (size_t)T.pnode_off[T.S]));
@@ -321,6 +356,7 @@ fp_status build_device(fp_handle *h) {
   for (double **v : {&h->ce, &h->cy, &h->calpha}) TRY(dalloc(h, v, nc));
   TRY(dalloc(h, &h->partial, 2 * RED_BLOCKS));
   TRY(dalloc(h, &h->sc, SC_N));
+  TRY(dalloc(h, &h->ir_prev, 1));
   TRY(dalloc(h, &h->red_counter, 4));
   TRY(dalloc(h, &h->fl, FL_N));
   TRY(dalloc(h, &h->fl_zero, FL_N));
@@ -350,7 +386,7 @@ fp_status build_device(fp_handle *h) {
     TRY(dalloc(h, &h->xb, (size_t)CH * MLP_NIN));
     TRY(dalloc(h, &h->fscale, 1));
     TRY(dalloc(h, &h->loss_rows, CH)); TRY(dalloc(h, &h->loss_acc, 1));
-    TRY(dalloc(h, &h->fsum, 2)); TRY(dalloc(h, &h->nrm, 2));
+    TRY(dalloc(h, &h->fsum, 2)); TRY(dalloc(h, &h->nrm, 4));
     TRY(dalloc(h, &h->idx_dev, CH)); TRY(dalloc(h, &h->choose_flag, 1));
     for (double **v : {&h->lam_prev2, &h->lam_b, &h->r_b}) TRY(dalloc(h, v, (size_t)nl));
     CK(cudaMemsetAsync(h->lam_prev2, 0, nl * sizeof(double), h->stream));
@@ -382,27 +418,49 @@ fp_status build_device(fp_handle *h) {
   }
   CK(cudaMallocHost(&h->h_fl, FL_N * sizeof(int)));
   CK(cudaMallocHost(&h->h_sc, SC_N * sizeof(double)));
+  CK(cudaMallocHost(&h->h_stepv, ST_N * sizeof(double)));
+  CK(cudaMallocHost(&h->h_flinit, FL_N * sizeof(int)));
+  for (int i = 0; i < FL_N; ++i) h->h_flinit[i] = 0;
+  h->h_flinit[FL_MAXIT] = h->P.max_it;
+  for (int i = 0; i < ST_N; ++i) h->h_stepv[i] = 0.0;
+  TRY(dalloc(h, &h->stepv, ST_N));
+  for (auto &c : h->cap) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
   for (auto &e : h->ev) CK(cudaEventCreate(&e));
   return FP_OK;
 }
 
 // ------------------------------ building blocks -------------------------------------
-fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac, const void *linv,
-                       double *x, int mmax, const int *done) {
+// The blocked solve's launch shape made legal for the element size: a stage holds at least
+// one inverse block and one column of the widest band; the ring fits the shared memory of
+// one CTA (and of cps CTAs per SM).
+fp_handle::SolveShape legal_shape(const fp_handle *h, fp_handle::SolveShape sh, bool fp32) {
+  const int esz = fp32 ? 4 : 8;
+  sh.chunk = std::max(sh.chunk, 1024 * esz);
+  sh.chunk = std::max(sh.chunk, (std::max(h->ldmax, h->T.LDH) * esz + 1023) / 1024 * 1024);
+  while (sh.wpc > 1 && (size_t)sh.wpc * 3 * (sh.chunk + 8) > 200 * 1024) sh.wpc >>= 1;
+  if (sh.cps < 1) sh.cps = 1;
+  while (sh.cps > 1 && (size_t)sh.cps * sh.wpc * 3 * (sh.chunk + 8) > 220 * 1024) --sh.cps;
+  return sh;
+}
+
+// shape from the task count when nothing was tuned: warps per CTA double while every SM
+// still gets two CTAs' worth of tasks; options pinned by the caller win
+fp_handle::SolveShape default_shape(const fp_handle *h, int ntask) {
+  fp_handle::SolveShape sh{h->solve_wpc, h->solve_chunk ? h->solve_chunk : 8192, h->solve_cps ? h->solve_cps : 1};
+  if (sh.wpc <= 0) {
+    sh.wpc = 1;
+    while (sh.wpc < 8 && ntask >= 2 * sh.wpc * h->num_sms) sh.wpc *= 2;
+  }
+  return sh;
+}
+
+fp_status launch_solve_shaped(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac,
+                              const void *linv, double *x, int mmax, const int *done, fp_handle::SolveShape sh) {
   CK(cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream));
   if (h->solve_kernel == 1 && linv) {
-    // stage size: at least one inverse block and one column of the widest band
-    const int esz = fp32 ? 4 : 8;
-    int chunk = std::max(h->solve_chunk, 1024 * esz);
-    chunk = std::max(chunk, (std::max(h->ldmax, h->T.LDH) * esz + 1023) / 1024 * 1024);
-    int wpc = h->solve_wpc;
-    if (wpc <= 0) {
-      wpc = 1;
-      while (wpc < 8 && ntask >= 2 * wpc * h->num_sms) wpc *= 2;
-    }
-    while (wpc > 1 && (size_t)wpc * 3 * (chunk + 8) > 200 * 1024) wpc >>= 1;
-    const int grid = std::max(1, std::min(h->num_sms, (ntask + wpc - 1) / wpc));
-    CK(launch_band_solve_blk(fp32, mmax, grid, wpc, chunk, h->stream, tasks, ntask, fac, linv, x, h->counter,
+    sh = legal_shape(h, sh, fp32);
+    const int grid = std::max(1, std::min(sh.cps * h->num_sms, (ntask + sh.wpc - 1) / sh.wpc));
+    CK(launch_band_solve_blk(fp32, mmax, grid, sh.wpc, sh.chunk, h->stream, tasks, ntask, fac, linv, x, h->counter,
                              h->status, done));
   } else {
     int wpc = ntask >= 4 * h->num_sms ? 4 : (ntask >= 2 * h->num_sms ? 2 : 1);
@@ -413,7 +471,18 @@ fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask
   return FP_OK;
 }
 
+fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac, const void *linv,
+                       double *x, int mmax, const int *done) {
+  const fp_handle::SolveShape sh = h->shape.wpc > 0 ? h->shape : default_shape(h, ntask);
+  return launch_solve_shaped(h, fp32, tasks, ntask, fac, linv, x, mmax, done, sh);
+}
+
 fp_status next_event(fp_handle *h, cudaEvent_t *e) {
+  if (h->capturing) {  // events recorded by the graph: created before the capture began
+    if (h->gev_used == h->gev.size()) { h->err = "graph profiling: out of events"; return FP_ERR_STATE; }
+    *e = h->gev[h->gev_used++];
+    return FP_OK;
+  }
   if (h->ev_used == h->ev_pool.size()) {
     cudaEvent_t ne;
     CK(cudaEventCreate(&ne));
@@ -427,15 +496,20 @@ fp_status solve_local(fp_handle *h, bool dirichlet, double *x, const int *done) 
   const void *fac = dirichlet ? h->facD : h->facN;
   const BandTask *tasks = dirichlet ? h->tasksD : h->tasksN;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h->profiling) {
-    h->pending.push_back({dirichlet ? 1 : 0, h->ev_used});
+  // launches inside a conditional body are not timed (a body may not hold event nodes)
+  const bool timed = h->profiling && !h->in_body;
+  const unsigned evflags = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (timed) {
     TRY(next_event(h, &e0));
     TRY(next_event(h, &e1));
-    CK(cudaEventRecord(e0, h->stream));
+    CK(cudaEventRecordWithFlags(e0, h->stream, evflags));
   }
   const void *linv = dirichlet ? h->linvD : h->linvN;
   TRY(launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, linv, x, h->mmax, done));
-  if (h->profiling) CK(cudaEventRecord(e1, h->stream));
+  if (timed) {
+    CK(cudaEventRecordWithFlags(e1, h->stream, evflags));
+    (h->capturing ? h->gpending : h->pending).push_back({dirichlet ? 1 : 0, e0, e1});
+  }
   return FP_OK;
 }
 
@@ -444,10 +518,10 @@ fp_status solve_local(fp_handle *h, bool dirichlet, double *x, const int *done) 
 fp_status collect_profile(fp_handle *h) {
   for (auto &pr : h->pending) {
     float ms = 0;
-    CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]));
+    CK(cudaEventElapsedTime(&ms, pr.e0, pr.e1));
     if (ms > 0.02f) {
-      h->prof_launches[pr.first] += 1;
-      h->prof_ms[pr.first] += ms;
+      h->prof_launches[pr.kind] += 1;
+      h->prof_ms[pr.kind] += ms;
     }
   }
   h->pending.clear();
@@ -465,13 +539,15 @@ fp_status solve_refined(fp_handle *h, const double *b, double *x, int sweeps, co
   // adaptive: the skip flag fl_ir[FL_IRSKIP] turns the remaining sweeps into no-ops
   int *skip = h->fl_ir + FL_IRSKIP;
   CK(cudaMemsetAsync(skip, 0, sizeof(int), h->stream));
+  CK(cudaMemsetAsync(h->ir_prev, 0, sizeof(double), h->stream));
   for (int it = 0; it < sweeps; ++it) {
-    k_residual_N<<<h->T.S, 256, 0, h->stream>>>(h->D, h->csr_val, b, x, h->XR, skip);
+    k_residual_N<<<h->T.S, 256, 0, h->stream>>>(h->D, h->sell_val, b, x, h->XR, skip);
     CKL();
     TRY(solve_local(h, false, h->XR, skip));
     k_local_add<<<1184, 256, 0, h->stream>>>(x, h->XR, nv, skip);
     k_ir_check<<<RED_BLOCKS, 256, 0, h->stream>>>(x, h->XR, nv, h->ir_eps * h->ir_eps, h->partial,
-                                                  h->red_counter + 2, h->fl_ir);
+                                                  h->red_counter + 2, h->fl_ir, h->ir_prev,
+                                                  h->ir_stag * h->ir_stag);
     CKL();
   }
   (void)fl;
@@ -604,21 +680,20 @@ fp_status mlp_ensure_init(fp_handle *h, unsigned long long seed) {
   return FP_OK;
 }
 
-// features of step n from lambda^{n-1}, lambda^{n-2} and the source signal; fsum gets the
-// sums of squares of the last increment and of lambda^{n-1}
-fp_status build_features(fp_handle *h, double t_now) {
+// features of step n from lambda^{n-1}, lambda^{n-2} and the source signal (the ratio rho in
+// stepv[ST_RHO]); fsum gets the sums of squares of the last increment and of lambda^{n-1}
+fp_status build_features(fp_handle *h) {
   const int nl = h->T.n_lambda;
-  const double s0 = source_signal(h, t_now), s1 = h->sigma_hist[0], s2 = h->sigma_hist[1];
-  double rho = 1.0;
-  if (std::fabs(s1 - s2) > 1e-300) rho = std::max(-4.0, std::min(4.0, (s0 - s1) / (s1 - s2)));
   TRY(lincomb(h, h->t1, h->lam_prev, 1.0, h->lam_prev2, -1.0, nullptr));
   TRY(dot(h, h->t1, h->t1, OP_STORE, h->fsum, nullptr));
   TRY(dot(h, h->lam_prev, h->lam_prev, OP_STORE, h->fsum + 1, nullptr));
-  k_features<<<(nl + 255) / 256, 256, 0, h->stream>>>(nl, h->lam_prev, h->lam_prev2, h->fsum, rho, h->xy_rows,
+  k_features<<<(nl + 255) / 256, 256, 0, h->stream>>>(nl, h->lam_prev, h->lam_prev2, h->fsum, h->stepv, h->xy_rows,
                                                       h->kind_rows, h->comp_rows, h->Xf, h->fscale);
   CKL();
   return FP_OK;
 }
+
+fp_status choose_nb(fp_handle *h, bool dbl, const BandTask *tasks, void *buf, int *nb_out);
 
 template <typename T>
 fp_status factor_T(fp_handle *h) {
@@ -643,9 +718,9 @@ fp_status factor_T(fp_handle *h) {
     cudaError_t e = cudaMalloc(&tL, (size_t)h->linv_total * sizeof(double));
     if (e != cudaSuccess) { cudaFree(tN); h->err = cudaGetErrorString(e); return FP_ERR_OOM; }
     int NB = 32;
-    while (NB > 4 && (size_t)NB * (h->ldmax + 1) * sizeof(double) > 200 * 1024) NB /= 2;
+    fp_status st = choose_nb(h, true, h->tasksN, tN, &NB);
+    h->tuning.factor_nb = NB;
     const size_t smem = (size_t)NB * (h->ldmax + 1) * sizeof(double);
-    fp_status st = FP_OK;
     for (int mode = 0; mode < 2 && st == FP_OK; ++mode) {
       T *dstF = (T *)(mode == 0 ? h->facN : h->facD);
       T *dstL = (T *)(mode == 0 ? h->linvN : h->linvD);
@@ -662,10 +737,11 @@ fp_status factor_T(fp_handle *h) {
     cudaFree(tL);
     return st;
   }
+  int NB = 32;
+  TRY(choose_nb(h, !f32, h->tasksN, fN, &NB));
+  h->tuning.factor_nb = NB;
   CK(launch_csr_to_band(f32, h->D, h->csr_val, fN, 0, h->stream));
   CK(launch_csr_to_band(f32, h->D, h->csr_val, fD, 1, h->stream));
-  int NB = 32;
-  while (NB > 4 && (size_t)NB * (h->ldmax + 1) * sizeof(T) > 200 * 1024) NB /= 2;
   const size_t smem = (size_t)NB * (h->ldmax + 1) * sizeof(T);
   CK(launch_band_factor(f32, h->tasksN, h->ntask, fN, NB, h->status, smem, h->stream));
   CK(launch_band_factor(f32, h->tasksD, h->ntask, fD, NB, h->status, smem, h->stream));
@@ -697,6 +773,91 @@ fp_status factor_coarse(fp_handle *h) {
   return FP_OK;
 }
 
+// ----------------------------------- autotuner -----------------------------------------
+// Panel width of the factorisation: each candidate factorises the 2 x num_sms largest tasks
+// (the task list is sorted by cost) after a fresh copy of the band; the fastest is kept.
+fp_status choose_nb(fp_handle *h, bool dbl, const BandTask *tasks, void *buf, int *nb_out) {
+  const size_t esz = dbl ? 8 : 4;
+  auto fits = [&](int nb) { return (size_t)nb * (h->ldmax + 1) * esz <= 200 * 1024; };
+  if (h->factor_nb > 0) {
+    int nb = h->factor_nb;
+    while (nb > 4 && !fits(nb)) nb /= 2;
+    *nb_out = nb;
+    return FP_OK;
+  }
+  int nb = 64;
+  while (nb > 4 && !fits(nb)) nb /= 2;
+  if (nb > 32) nb = 32;
+  if (!h->autotune) { *nb_out = nb; return FP_OK; }
+  const int sub = std::min(h->ntask, 2 * h->num_sms);
+  cudaEvent_t e0 = h->ev[4], e1 = h->ev[5];
+  float best = 1e30f;
+  for (int cand : {8, 16, 32, 64}) {
+    if (!fits(cand)) continue;
+    CK(launch_csr_to_band(!dbl, h->D, h->csr_val, buf, 0, h->stream));
+    CK(cudaEventRecord(e0, h->stream));
+    CK(launch_band_factor(!dbl, tasks, sub, buf, cand, h->status, (size_t)cand * (h->ldmax + 1) * esz, h->stream));
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; nb = cand; }
+  }
+  h->tuning.factor_ms = best;
+  *nb_out = nb;
+  return FP_OK;
+}
+
+// Launch shape of the blocked solves: every legal (warps per CTA, stage bytes, CTAs per SM)
+// is timed on a Neumann solve of all subdomains (a zero vector stays zero, so the scratch
+// vector is left as it was); the fastest is kept.  Options set by the caller stay fixed.
+fp_status autotune_solve(fp_handle *h) {
+  const bool fp32 = h->P.precision == FP_PREC_MIXED;
+  const fp_handle::SolveShape def = legal_shape(h, default_shape(h, h->ntask), fp32);
+  h->shape = def;
+  h->tuning.candidates = 0;
+  if (h->autotune && h->solve_kernel == 1) {
+    std::vector<fp_handle::SolveShape> cands;
+    for (int wpc : {1, 2, 4, 8}) {
+      if (h->solve_wpc && wpc != h->solve_wpc) continue;
+      for (int chunk : {4096, 8192, 16384, 32768}) {
+        if (h->solve_chunk && chunk != h->solve_chunk) continue;
+        for (int cps : {1, 2}) {
+          if (h->solve_cps && cps != h->solve_cps) continue;
+          const fp_handle::SolveShape sh = legal_shape(h, {wpc, chunk, cps}, fp32);
+          if (sh.wpc != wpc || sh.cps != cps) continue;
+          bool dup = false;
+          for (auto &c : cands) dup |= c.wpc == sh.wpc && c.chunk == sh.chunk && c.cps == sh.cps;
+          if (!dup) cands.push_back(sh);
+        }
+      }
+    }
+    const long long nv = h->T.vec_off[h->T.S];
+    cudaEvent_t e0 = h->ev[4], e1 = h->ev[5];
+    float best = 1e30f;
+    for (const auto &sh : cands) {
+      float tot = 0.0f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaMemsetAsync(h->XB, 0, nv * sizeof(double), h->stream));
+        CK(cudaEventRecord(e0, h->stream));
+        TRY(launch_solve_shaped(h, fp32, h->tasksN, h->ntask, h->facN, h->linvN, h->XB, h->mmax, nullptr, sh));
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tot += ms;
+      }
+      ++h->tuning.candidates;
+      if (tot / 2 < best) { best = tot / 2; h->shape = sh; }
+    }
+    h->tuning.solve_ms = best;
+  }
+  h->tuning.solve_wpc = h->shape.wpc;
+  h->tuning.solve_chunk = h->shape.chunk;
+  h->tuning.solve_ctas_per_sm = h->shape.cps;
+  return FP_OK;
+}
+
 fp_status check_status(fp_handle *h) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -704,6 +865,303 @@ fp_status check_status(fp_handle *h) {
   if (st == DS_ZERO_PIVOT) { h->err = "zero or non-finite pivot in a local LDL^T factorisation"; return FP_ERR_BREAKDOWN; }
   if (st == DS_TIMEOUT) { h->err = "a bounded device wait gave up (TMA copy did not complete)"; return FP_ERR_TIMEOUT; }
   if (st) { h->err = "device status " + std::to_string(st); return FP_ERR_BREAKDOWN; }
+  return FP_OK;
+}
+
+// ----------------------------------- one time step -----------------------------------
+// A step is recorded by pieces shared by the graph path and the stream path:
+// step_prologue (right-hand side, d, lambda_00, lambda_0, the reference residual, r_0 and
+// the learned guess), the Krylov loop, and step_recovery.  With use_graph the three are
+// captured once into a CUDA graph whose Krylov loop is two nested conditional WHILE nodes,
+// so a whole step is one graph launch and no host round trip until its end.
+
+fp_status record_event(fp_handle *h, cudaEvent_t e) {
+  CK(cudaEventRecordWithFlags(e, h->stream, h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+  return FP_OK;
+}
+
+fp_status step_prologue(fp_handle *h, bool use_learned) {
+  Topology &T = h->T;
+  const int nl = T.n_lambda;
+  const bool mixed = h->P.precision == FP_PREC_MIXED;
+  cudaStream_t s = h->stream;
+  // per-step scalars and flags from pinned host memory (read when this point executes)
+  CK(cudaMemcpyAsync(h->stepv, h->h_stepv, ST_N * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->fl, h->h_flinit, FL_N * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->sc + SC_TOL2, h->stepv + ST_TOL2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+  // right-hand side f, d = B K^+ f (refined), e = R^T f
+  double *fbuf = mixed ? h->XF : h->X2;
+  k_rhs<<<T.S, 256, 0, s>>>(h->D, h->DP, h->fstat, h->Zn, h->E0n, h->Reta, h->stepv, fbuf, h->ce);
+  CKL();
+  TRY(solve_refined(h, fbuf, h->X2, h->ir_sweeps, nullptr));
+  k_gather<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->X2, h->d, nullptr);
+  CKL();
+  // lambda_00 = G (G^T G)^{-1} e ; lambda_0 = lambda_00 + P lambda^{n-1}
+  if (T.NF) {
+    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->ce, h->calpha, T.nH, nullptr);
+    k_Gcomb<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->calpha, nullptr, 1.0, h->lam00, nullptr);
+    CKL();
+  } else {
+    CK(cudaMemsetAsync(h->lam00, 0, nl * sizeof(double), s));
+  }
+  TRY(apply_P(h, h->lam_prev, h->t1, h->fl_zero));
+  TRY(lincomb(h, h->lam, h->lam00, 1.0, h->t1, 1.0, nullptr));
+  // reference ||P(d - F lambda_00)|| (guess independent)
+  if (T.NF) {
+    TRY(apply_F(h, h->lam00, h->t2, h->fl_zero));
+    TRY(lincomb(h, h->t2, h->d, 1.0, h->t2, -1.0, nullptr));
+    TRY(apply_P(h, h->t2, h->t2, h->fl_zero));
+    TRY(dot(h, h->t2, h->t2, OP_STORE, h->sc + SC_REF2, nullptr));
+  } else {
+    TRY(dot(h, h->d, h->d, OP_STORE, h->sc + SC_REF2, nullptr));
+  }
+  // r_0 = P(d - F lambda_0) with the accurate operator
+  TRY(apply_F(h, h->lam, h->q, h->fl_zero));
+  TRY(lincomb(h, h->r, h->d, 1.0, h->q, -1.0, nullptr));
+  TRY(apply_P(h, h->r, h->r, h->fl_zero));
+  // learned lambda_0: the MLP predicts the next increment; the judge keeps whichever guess
+  // has the smaller true projected residual (lambda^{n-1} is the fallback)
+  if (use_learned) {
+    TRY(build_features(h));
+    TRY(mlp_forward(h, h->Xf, nl, h->mout));
+    k_guess<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam_prev, h->mout, h->Xf, h->fsum, h->t2);
+    CKL();
+    TRY(apply_P(h, h->t2, h->t2, h->fl_zero));
+    TRY(lincomb(h, h->lam_b, h->lam00, 1.0, h->t2, 1.0, nullptr));
+    TRY(apply_F(h, h->lam_b, h->q, h->fl_zero));
+    TRY(lincomb(h, h->r_b, h->d, 1.0, h->q, -1.0, nullptr));
+    TRY(apply_P(h, h->r_b, h->r_b, h->fl_zero));
+    TRY(dot(h, h->r, h->r, OP_STORE, h->nrm, nullptr));
+    TRY(dot(h, h->r_b, h->r_b, OP_STORE, h->nrm + 1, nullptr));
+    const double *na = h->nrm, *nb = h->nrm + 1;
+    if (h->judge == 1) {
+      // preconditioned residual norms: (P r, P M^-1 P r) approximates the F-norm of the error,
+      // the quantity the convergence bound of Algorithm 1 starts from
+      TRY(apply_M(h, h->r, h->t1, h->fl_zero));
+      TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
+      TRY(dot(h, h->r, h->t1, OP_STORE, h->nrm + 2, nullptr));
+      TRY(apply_M(h, h->r_b, h->t1, h->fl_zero));
+      TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
+      TRY(dot(h, h->r_b, h->t1, OP_STORE, h->nrm + 3, nullptr));
+      na = h->nrm + 2;
+      nb = h->nrm + 3;
+    }
+    k_choose<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam, h->r, h->lam_b, h->r_b, na, nb, h->choose_flag);
+    CKL();
+  }
+  return FP_OK;
+}
+
+// z = P M^{-1} r, p = z, (r, z): the start of Algorithm 1 and of every restart
+fp_status pcg_start(fp_handle *h) {
+  TRY(dot(h, h->r, h->r, OP_RNORM0, nullptr, nullptr));
+  TRY(apply_M(h, h->r, h->z, h->fl_zero));
+  TRY(apply_P(h, h->z, h->z, h->fl_zero));
+  CK(cudaMemcpyAsync(h->p, h->z, h->T.n_lambda * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  TRY(dot(h, h->r, h->z, OP_RZ_INIT, nullptr, nullptr));
+  return FP_OK;
+}
+
+// one iteration of Algorithm 1; F may use unrefined FP32 solves (mixed precision); every
+// kernel is a no-op once the device flag fl[FL_DONE] is set
+fp_status pcg_iteration(fp_handle *h) {
+  const int nl = h->T.n_lambda;
+  cudaStream_t s = h->stream;
+  TRY(apply_F(h, h->p, h->q, h->fl, false));
+  TRY(apply_P(h, h->q, h->q, h->fl));
+  TRY(dot(h, h->p, h->q, OP_PQ, nullptr, h->fl));
+  k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
+  CKL();
+  TRY(apply_M(h, h->r, h->z, h->fl));
+  TRY(apply_P(h, h->z, h->z, h->fl));
+  TRY(dot(h, h->r, h->z, OP_RZ, nullptr, h->fl));
+  k_pcg_pupdate<<<(nl + 255) / 256, 256, 0, s>>>(h->p, h->z, nl, h->sc, h->fl);
+  CKL();
+  return FP_OK;
+}
+
+// ||P(d - F lambda)||^2 into sc[SC_TRUE2] with the accurate operator; leaves F lambda in t2,
+// P(d - F lambda) in t1 and K^+ B^T lambda in xsol(h)
+fp_status true_residual(fp_handle *h) {
+  TRY(apply_F(h, h->lam, h->t2, h->fl_zero));
+  TRY(lincomb(h, h->t1, h->d, 1.0, h->t2, -1.0, nullptr));
+  TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
+  TRY(dot(h, h->t1, h->t1, OP_STORE, h->sc + SC_TRUE2, nullptr));
+  return FP_OK;
+}
+
+// Algorithm 1 driven from the host: chunks of pcg_chunk iterations between polls of the
+// device flags, restarted from the true residual until the true residual meets tol
+fp_status krylov_stream(fp_handle *h, int *restarts_out) {
+  cudaStream_t s = h->stream;
+  const double tol2 = h->P.tol * h->P.tol;
+  int restarts = 0;
+  for (;;) {
+    TRY(pcg_start(h));
+    for (int it = 0; it < h->P.max_it; it += h->pcg_chunk) {
+      for (int c = 0; c < h->pcg_chunk; ++c) TRY(pcg_iteration(h));
+      CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h->h_fl[FL_DONE]) break;
+    }
+    TRY(true_residual(h));
+    CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const bool ok = h->h_sc[SC_TRUE2] <= tol2 * h->h_sc[SC_REF2];
+    if (ok || h->h_fl[FL_STATUS] || restarts >= h->max_restarts || h->h_fl[FL_ITER] >= h->P.max_it) break;
+    // restart: r = true residual, keep the iteration count
+    ++restarts;
+    CK(cudaMemcpyAsync(h->r, h->t1, h->T.n_lambda * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(h->fl + FL_DONE, 0, sizeof(int), s));
+  }
+  *restarts_out = restarts;
+  return FP_OK;
+}
+
+// Adds, at the capture position of h->stream, a conditional WHILE node: `arm` launches the
+// kernel that sets its first condition value, `body` records the body on capture stream
+// cap[depth] (the body's last kernel sets the condition for the next round).
+using CondFn = std::function<fp_status(cudaGraphConditionalHandle)>;
+fp_status capture_while(fp_handle *h, int depth, const CondFn &arm, const CondFn &body) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  cudaGraph_t cg = nullptr;
+  CK(cudaStreamGetCaptureInfo(h->stream, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
+  if (cst != cudaStreamCaptureStatusActive || depth < 1 || depth > 2) {
+    h->err = "capture_while: stream not capturing";
+    return FP_ERR_STATE;
+  }
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, cg, 0, 0));
+  TRY(arm(hc));
+  const cudaGraphNode_t *dp = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(h->stream, &cst, nullptr, &cg, &dp, nullptr, &nd));
+  std::vector<cudaGraphNode_t> deps(dp, dp + nd);
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hc;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, cg, deps.data(), nullptr, deps.size(), &np));
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+  cudaStream_t outer = h->stream, bs = h->cap[depth];
+  CK(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int was_in_body = h->in_body;
+  h->stream = bs;
+  h->in_body = 1;
+  const fp_status st = body(hc);
+  h->in_body = was_in_body;
+  h->stream = outer;
+  cudaGraph_t ended = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(bs, &ended);
+  if (st != FP_OK) return st;
+  if (e != cudaSuccess) { h->err = std::string("capture of a loop body: ") + cudaGetErrorString(e); return FP_ERR_CUDA; }
+  CK(cudaStreamUpdateCaptureDependencies(outer, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return FP_OK;
+}
+
+// Algorithm 1 with restarts as two nested WHILE nodes (recorded while capturing)
+fp_status krylov_graph(fp_handle *h) {
+  const int nl = h->T.n_lambda;
+  const int max_body = (h->P.max_it + h->pcg_chunk - 1) / h->pcg_chunk + 1;
+  const CondFn arm_outer = [h](cudaGraphConditionalHandle hc) -> fp_status {
+    k_loop_arm_outer<<<1, 1, 0, h->stream>>>(hc, h->fl);
+    CKL();
+    return FP_OK;
+  };
+  const CondFn arm_inner = [h](cudaGraphConditionalHandle hc) -> fp_status {
+    k_loop_arm_inner<<<1, 1, 0, h->stream>>>(hc, h->fl);
+    CKL();
+    return FP_OK;
+  };
+  const CondFn body_inner = [h, max_body](cudaGraphConditionalHandle hc) -> fp_status {
+    for (int c = 0; c < h->pcg_chunk; ++c) TRY(pcg_iteration(h));
+    k_loop_inner<<<1, 1, 0, h->stream>>>(hc, h->fl, max_body);
+    CKL();
+    return FP_OK;
+  };
+  const CondFn body_outer = [&](cudaGraphConditionalHandle hc) -> fp_status {
+    // restart: r = true residual of the previous round (no-op in the first round)
+    k_copy_if<<<grid_for(nl, 256), 256, 0, h->stream>>>(h->r, h->t1, nl, h->fl + FL_PENDING);
+    CKL();
+    TRY(pcg_start(h));
+    TRY(capture_while(h, 2, arm_inner, body_inner));
+    TRY(true_residual(h));
+    k_loop_outer<<<1, 1, 0, h->stream>>>(hc, h->fl, h->sc, h->max_restarts);
+    CKL();
+    return FP_OK;
+  };
+  return capture_while(h, 1, arm_outer, body_outer);
+}
+
+// recovery: alpha = (G^T G)^{-1} G^T (F lambda - d); x_s = K^+ f - K^+ B^T lambda + R alpha
+fp_status step_recovery(fp_handle *h) {
+  Topology &T = h->T;
+  cudaStream_t s = h->stream;
+  if (T.NF) {
+    TRY(lincomb(h, h->t1, h->t2, 1.0, h->d, -1.0, nullptr));
+    k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr);
+    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->cy, h->calpha, T.nH, nullptr);
+    CKL();
+  }
+  k_recover<<<T.S, 256, 0, s>>>(h->D, h->DP, h->X2, xsol(h), h->calpha, h->U, h->XI, h->ETA, h->PP, h->Reta);
+  CKL();
+  return FP_OK;
+}
+
+void drop_graph(fp_handle *h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  h->gpending.clear();
+}
+
+// captures prologue + Krylov loop + recovery of a step into h->gexec
+fp_status capture_step(fp_handle *h, bool use_learned) {
+  drop_graph(h);
+  // events of the timed prologue launches: at most 4 accurate solves of 1 + ir_sweeps launches
+  const size_t need = h->profiling ? 2 * 4 * (size_t)(1 + h->ir_sweeps) : 0;
+  while (h->gev.size() < need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    h->gev.push_back(e);
+  }
+  h->gev_used = 0;
+  cudaStream_t user = h->stream;
+  CK(cudaStreamBeginCapture(h->cap[0], cudaStreamCaptureModeThreadLocal));
+  h->stream = h->cap[0];
+  h->capturing = 1;
+  fp_status st = step_prologue(h, use_learned);
+  if (st == FP_OK) st = record_event(h, h->ev[1]);
+  if (st == FP_OK) st = krylov_graph(h);
+  if (st == FP_OK) st = record_event(h, h->ev[2]);
+  if (st == FP_OK) st = step_recovery(h);
+  h->capturing = 0;
+  h->stream = user;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap[0], &g);
+  if (st != FP_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    h->gpending.clear();
+    if (st == FP_OK) { h->err = std::string("capture of a time step: ") + cudaGetErrorString(e); st = FP_ERR_CUDA; }
+    cudaGetLastError();
+    return st;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&h->gexec, g, 0);
+  if (ei != cudaSuccess) {
+    cudaGraphDestroy(g);
+    h->gexec = nullptr;
+    h->gpending.clear();
+    h->err = std::string("instantiating the step graph: ") + cudaGetErrorString(ei);
+    return FP_ERR_CUDA;
+  }
+  h->graph = g;
+  h->gkey = use_learned ? 1 : 0;
+  h->gdirty = 0;
   return FP_OK;
 }
 
@@ -766,6 +1224,10 @@ fp_status fp_assemble(fp_handle *h) {
   CK(cudaMemsetAsync(h->E0n, 0, T.pnode_off[T.S] * sizeof(double), h->stream));
   k_assemble<<<T.S, 256, 0, h->stream>>>(h->D, h->DP, h->csr_val, h->fstat, h->Zn, h->E0n);
   CKL();
+  if (h->sell_val) {
+    k_csr_to_sell<<<T.S, 256, 0, h->stream>>>(h->D, h->csr_val, h->sell_val);
+    CKL();
+  }
   // initial state: R eta^0 = (eta_0, phi_i) (L2 projection), lambda^0 = 0
   CK(cudaMemcpyAsync(h->Reta, h->E0n, T.pnode_off[T.S] * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemsetAsync(h->lam_prev, 0, std::max(T.n_lambda, 1) * sizeof(double), h->stream));
@@ -789,7 +1251,10 @@ fp_status fp_factor(fp_handle *h) {
   TRY(h->P.precision == FP_PREC_MIXED ? factor_T<float>(h) : factor_T<double>(h));
   TRY(factor_coarse(h));
   TRY(check_status(h));
+  TRY(autotune_solve(h));
+  TRY(check_status(h));
   h->stage = 2;
+  h->gdirty = 1;
   return FP_OK;
 }
 
@@ -800,124 +1265,34 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   const int nl = T.n_lambda;
   const int n = h->step_n + 1;
   const double t_now = n * h->P.tau;
-  const bool mixed = h->P.precision == FP_PREC_MIXED;
   cudaStream_t s = h->stream;
-  CK(cudaEventRecord(h->ev[0], s));
-  // flags and scalars
-  int hfl[FL_N] = {0, 0, 0, h->P.max_it, 0, 0, 0, 0};
-  CK(cudaMemcpyAsync(h->fl, hfl, sizeof hfl, cudaMemcpyHostToDevice, s));
+  // per-step scalars: t_n, the extrapolation ratio of the source signal, tol^2
   const double tol2 = h->P.tol * h->P.tol;
-  CK(cudaMemcpyAsync(h->sc + SC_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
-  // right-hand side f, d = B K^+ f (refined), e = R^T f
-  double *fbuf = mixed ? h->XF : h->X2;
-  k_rhs<<<T.S, 256, 0, s>>>(h->D, h->DP, h->fstat, h->Zn, h->E0n, h->Reta, t_now, fbuf, h->ce);
-  CKL();
-  TRY(solve_refined(h, fbuf, h->X2, h->ir_sweeps, nullptr));
-  k_gather<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->X2, h->d, nullptr);
-  CKL();
-  // lambda_00 = G (G^T G)^{-1} e ; lambda_0 = lambda_00 + P lambda^{n-1}
-  if (T.NF) {
-    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->ce, h->calpha, T.nH, nullptr);
-    k_Gcomb<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->calpha, nullptr, 1.0, h->lam00, nullptr);
-    CKL();
-  } else {
-    CK(cudaMemsetAsync(h->lam00, 0, nl * sizeof(double), s));
-  }
-  TRY(apply_P(h, h->lam_prev, h->t1, h->fl_zero));
-  TRY(lincomb(h, h->lam, h->lam00, 1.0, h->t1, 1.0, nullptr));
-  // reference ||P(d - F lambda_00)|| (guess independent)
-  if (T.NF) {
-    TRY(apply_F(h, h->lam00, h->t2, h->fl_zero));
-    TRY(lincomb(h, h->t2, h->d, 1.0, h->t2, -1.0, nullptr));
-    TRY(apply_P(h, h->t2, h->t2, h->fl_zero));
-    TRY(dot(h, h->t2, h->t2, OP_STORE, h->sc + SC_REF2, nullptr));
-  } else {
-    TRY(dot(h, h->d, h->d, OP_STORE, h->sc + SC_REF2, nullptr));
-  }
-  // r_0 = P(d - F lambda_0) with the accurate operator
-  TRY(apply_F(h, h->lam, h->q, h->fl_zero));
-  TRY(lincomb(h, h->r, h->d, 1.0, h->q, -1.0, nullptr));
-  TRY(apply_P(h, h->r, h->r, h->fl_zero));
-  // learned lambda_0: the MLP predicts the next increment; the judge keeps whichever guess
-  // has the smaller true projected residual (lambda^{n-1} is the fallback)
+  const double s0 = source_signal(h, t_now), s1 = h->sigma_hist[0], s2 = h->sigma_hist[1];
+  double rho = 1.0;
+  if (std::fabs(s1 - s2) > 1e-300) rho = std::max(-4.0, std::min(4.0, (s0 - s1) / (s1 - s2)));
+  h->h_stepv[ST_T] = t_now;
+  h->h_stepv[ST_RHO] = rho;
+  h->h_stepv[ST_TOL2] = tol2;
+  h->h_flinit[FL_STAGWIN] = h->stag_window;
   const bool use_learned = h->learned_use && h->mlp_ready && h->hist >= 2;
-  bool features_built = false;
-  if (use_learned) {
-    TRY(build_features(h, t_now));
-    features_built = true;
-    TRY(mlp_forward(h, h->Xf, nl, h->mout));
-    k_guess<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam_prev, h->mout, h->Xf, h->fsum, h->t2);
-    CKL();
-    TRY(apply_P(h, h->t2, h->t2, h->fl_zero));
-    TRY(lincomb(h, h->lam_b, h->lam00, 1.0, h->t2, 1.0, nullptr));
-    TRY(apply_F(h, h->lam_b, h->q, h->fl_zero));
-    TRY(lincomb(h, h->r_b, h->d, 1.0, h->q, -1.0, nullptr));
-    TRY(apply_P(h, h->r_b, h->r_b, h->fl_zero));
-    TRY(dot(h, h->r, h->r, OP_STORE, h->nrm, nullptr));
-    TRY(dot(h, h->r_b, h->r_b, OP_STORE, h->nrm + 1, nullptr));
-    k_choose<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam, h->r, h->lam_b, h->r_b, h->nrm, h->nrm + 1, h->choose_flag);
-    CKL();
+  int restarts = 0;
+  if (h->use_graph) {
+    if (!h->gexec || h->gdirty || h->gkey != (use_learned ? 1 : 0)) TRY(capture_step(h, use_learned));
+    CK(cudaEventRecord(h->ev[0], s));
+    CK(cudaGraphLaunch(h->gexec, s));
+    h->pending.insert(h->pending.end(), h->gpending.begin(), h->gpending.end());
+  } else {
+    CK(cudaEventRecord(h->ev[0], s));
+    TRY(step_prologue(h, use_learned));
+    CK(cudaEventRecord(h->ev[1], s));
+    TRY(krylov_stream(h, &restarts));
+    CK(cudaEventRecord(h->ev[2], s));
+    TRY(step_recovery(h));
   }
-  CK(cudaEventRecord(h->ev[1], s));
-  // Algorithm 1, restarted from the true residual until the true residual meets tol.
-  // Inside the loop F may use unrefined FP32 solves (mixed precision); every kernel is a
-  // no-op once the device flag `done` is set.
-  int restarts = 0, total_it = 0;
-  for (;;) {
-    TRY(dot(h, h->r, h->r, OP_RNORM0, nullptr, nullptr));
-    TRY(apply_M(h, h->r, h->z, h->fl_zero));
-    TRY(apply_P(h, h->z, h->z, h->fl_zero));
-    CK(cudaMemcpyAsync(h->p, h->z, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    TRY(dot(h, h->r, h->z, OP_RZ_INIT, nullptr, nullptr));
-    for (int it = 0; it < h->P.max_it; it += h->pcg_chunk) {
-      for (int c = 0; c < h->pcg_chunk; ++c) {
-        TRY(apply_F(h, h->p, h->q, h->fl, false));
-        TRY(apply_P(h, h->q, h->q, h->fl));
-        TRY(dot(h, h->p, h->q, OP_PQ, nullptr, h->fl));
-        k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
-        CKL();
-        TRY(apply_M(h, h->r, h->z, h->fl));
-        TRY(apply_P(h, h->z, h->z, h->fl));
-        TRY(dot(h, h->r, h->z, OP_RZ, nullptr, h->fl));
-        k_pcg_pupdate<<<(nl + 255) / 256, 256, 0, s>>>(h->p, h->z, nl, h->sc, h->fl);
-        CKL();
-      }
-      CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (h->h_fl[FL_DONE]) break;
-    }
-    // true residual with the accurate operator; leaves K^+ B^T lambda in xsol(h)
-    TRY(apply_F(h, h->lam, h->t2, h->fl_zero));
-    TRY(lincomb(h, h->t1, h->d, 1.0, h->t2, -1.0, nullptr));
-    TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
-    TRY(dot(h, h->t1, h->t1, OP_STORE, h->sc + SC_TRUE2, nullptr));
-    CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    total_it = h->h_fl[FL_ITER];
-    const bool ok = h->h_sc[SC_TRUE2] <= tol2 * h->h_sc[SC_REF2];
-    if (ok || h->h_fl[FL_STATUS] || restarts >= h->max_restarts || total_it >= h->P.max_it) break;
-    // restart: r = true residual, keep the iteration count
-    ++restarts;
-    CK(cudaMemcpyAsync(h->r, h->t1, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    const int zero = 0;
-    CK(cudaMemcpyAsync(h->fl + FL_DONE, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
-  }
-  h->restarts_last = restarts;
-  CK(cudaEventRecord(h->ev[2], s));
-  // recovery: alpha = (G^T G)^{-1} G^T (F lambda - d); x_s = K^+ f - K^+ B^T lambda + R alpha
-  if (T.NF) {
-    TRY(lincomb(h, h->t1, h->t2, 1.0, h->d, -1.0, nullptr));
-    k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr);
-    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->cy, h->calpha, T.nH, nullptr);
-    CKL();
-  }
-  k_recover<<<T.S, 256, 0, s>>>(h->D, h->DP, h->X2, xsol(h), h->calpha, h->U, h->XI, h->ETA, h->PP, h->Reta);
-  CKL();
   // training samples: features of this step and target (lambda^n - lambda^{n-1}) / s1
   if (h->learned_record && h->hist >= 2 && h->n_samples < h->cap_samples) {
-    if (!features_built) TRY(build_features(h, t_now));
+    if (!use_learned) TRY(build_features(h));
     const int per = std::min(h->record_per_step, nl);
     const int stride = std::max(1, nl / per);
     const int r0 = (int)(h->step_n % stride);
@@ -931,7 +1306,7 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   CK(cudaMemcpyAsync(h->lam_prev2, h->lam_prev, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->lam_prev, h->lam, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
   h->sigma_hist[1] = h->sigma_hist[0];
-  h->sigma_hist[0] = source_signal(h, t_now);
+  h->sigma_hist[0] = s0;
   h->hist += 1;
   CK(cudaEventRecord(h->ev[3], s));
   CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -944,6 +1319,8 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   }
   CK(cudaStreamSynchronize(s));
   TRY(collect_profile(h));
+  if (h->use_graph) restarts = h->h_fl[FL_RESTARTS];
+  h->restarts_last = restarts;
   float ms01 = 0, ms12 = 0, ms23 = 0;
   cudaEventElapsedTime(&ms01, h->ev[0], h->ev[1]);
   cudaEventElapsedTime(&ms12, h->ev[1], h->ev[2]);
@@ -962,6 +1339,8 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
     stats->guess_res_learned = h->last_res_learned;
     stats->rel_residual = ref2 > 0 ? std::sqrt(h->h_sc[SC_RNORM2] / ref2) : 0.0;
     stats->true_rel_residual = ref2 > 0 ? std::sqrt(h->h_sc[SC_TRUE2] / ref2) : 0.0;
+    stats->restarts = restarts;
+    stats->stagnations = h->h_fl[FL_NSTAG];
   }
   fp_status st = check_status(h);
   if (st) return st;
@@ -1217,24 +1596,40 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   auto bad = [&]() { h->err = "fp_set_option: bad value for " + k; return FP_ERR_INVALID; };
   if (k == "ir_sweeps") { if (v < 0 || v > 16) return bad(); h->ir_sweeps = v; }
   else if (k == "inner_ir") { if (v < 0 || v > 8) return bad(); h->inner_ir = v; }
+  else if (k == "ir_stag") { if (!(value >= 0.0) || value >= 1.0) return bad(); h->ir_stag = value; }
   else if (k == "ir_eps") { if (!(value >= 1e-17) || value > 1e-2) return bad(); h->ir_eps = value; }
   else if (k == "max_restarts") { if (v < 0 || v > 64) return bad(); h->max_restarts = v; }
   else if (k == "pcg_chunk") { if (v < 1 || v > 256) return bad(); h->pcg_chunk = v; }
   else if (k == "solve_kernel") { if (v < 0 || v > 1) return bad(); h->solve_kernel = v; }
   else if (k == "solve_wpc") { if (v < 0 || v > 8) return bad(); h->solve_wpc = v; }
   else if (k == "factor_fp64") { if (v < 0 || v > 1) return bad(); h->factor_fp64 = v; }
-  else if (k == "solve_chunk") { if (v < 4096 || v > 65536 || v % 1024) return bad(); h->solve_chunk = v; }
+  else if (k == "graph") { if (v < 0 || v > 1) return bad(); h->use_graph = v; }
+  else if (k == "stag_window") { if (v < 0 || v > 100000) return bad(); h->stag_window = v; }
+  else if (k == "judge") { if (v < 0 || v > 1) return bad(); h->judge = v; }
+  else if (k == "solve_chunk") { if (v != 0 && (v < 4096 || v > 65536 || v % 1024)) return bad(); h->solve_chunk = v; }
+  else if (k == "solve_cps") { if (v < 0 || v > 2) return bad(); h->solve_cps = v; }
+  else if (k == "factor_nb") { if (v != 0 && (v < 4 || v > 64 || v % 4)) return bad(); h->factor_nb = v; }
+  else if (k == "autotune") { if (v < 0 || v > 1) return bad(); h->autotune = v; }
   else { h->err = "fp_set_option: unknown key " + k; return FP_ERR_INVALID; }
+  h->gdirty = 1;
   return FP_OK;
 }
 
 fp_status fp_set_profiling(fp_handle *h, int on) {
   if (!h) return FP_ERR_INVALID;
   h->profiling = on ? 1 : 0;
+  h->gdirty = 1;
   h->prof_launches[0] = h->prof_launches[1] = 0;
   h->prof_ms[0] = h->prof_ms[1] = 0;
   h->pending.clear();
   h->ev_used = 0;
+  return FP_OK;
+}
+
+fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out) {
+  if (!h || !out) return FP_ERR_INVALID;
+  if (h->stage < 2) return FP_ERR_STATE;
+  *out = h->tuning;
   return FP_OK;
 }
 
@@ -1251,6 +1646,12 @@ const char *fp_last_error(const fp_handle *h) { return h ? h->err.c_str() : g_cr
 
 void fp_destroy(fp_handle *h) {
   if (!h) return;
+  drop_graph(h);
+  for (auto &c : h->cap)
+    if (c) cudaStreamDestroy(c);
+  for (auto &e : h->gev) cudaEventDestroy(e);
+  if (h->h_stepv) cudaFreeHost(h->h_stepv);
+  if (h->h_flinit) cudaFreeHost(h->h_flinit);
   for (void *p : h->allocs) cudaFree(p);
   if (h->h_fl) cudaFreeHost(h->h_fl);
   if (h->h_sc) cudaFreeHost(h->h_sc);

@@ -18,6 +18,8 @@ struct DevTpl {
   long long bnd, is_bnd;
   long long halo_ptr, halo_row, halo_ent;
   long long elem_dofs;
+  long long sell_ptr, sell_col, sell_src;  // sliced ELL of the Neumann matrix (see internal.h)
+  int nslice;
 };
 
 // Everything the kernels need about the partition, by pointer.
@@ -27,7 +29,7 @@ struct DevTopo {
   const int *pool;                  // integer pool for template arrays
   const int *sub_tpl;
   const double *sub_x0, *sub_y0, *sub_hx, *sub_hy;
-  const long long *vec_off, *fac_off, *csr_off, *unode_off, *pnode_off, *elem_off, *bsc_off;
+  const long long *vec_off, *fac_off, *csr_off, *unode_off, *pnode_off, *elem_off, *bsc_off, *sell_off;
   const int *sub_I0, *sub_J0;
   // interface
   const int *lam_sa, *lam_da, *lam_sb, *lam_db, *lam_kind;
@@ -68,8 +70,17 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // PCG state kept on the device: scalar slots, integer flags, reduction finalisers
-enum ScSlot { SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RNORM2, SC_REF2, SC_TOL2, SC_TMP, SC_TRUE2, SC_N = 16 };
-enum FlSlot { FL_DONE = 0, FL_ITER, FL_STATUS, FL_MAXIT, FL_IRSKIP, FL_IRSWEEPS, FL_N = 8 };
+enum ScSlot { SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RNORM2, SC_REF2, SC_TOL2, SC_TMP, SC_TRUE2, SC_RMIN,
+              SC_N = 16 };
+// FL_BODY, FL_RESTARTS, FL_PENDING: loop state of the per-step graph (bodies run in the
+// current WHILE loop, restarts taken, restart requested by the last true-residual check).
+// FL_STAG: iterations since the recursive residual last halved; FL_STAGWIN: the window after
+// which the loop stops for a restart (0: never); FL_NSTAG: such stops in this step.
+enum FlSlot { FL_DONE = 0, FL_ITER, FL_STATUS, FL_MAXIT, FL_IRSKIP, FL_IRSWEEPS, FL_BODY, FL_RESTARTS, FL_PENDING,
+              FL_STAG, FL_STAGWIN, FL_NSTAG, FL_N = 12 };
+// per-step scalars read by kernels from device memory (so one captured graph serves every
+// step): time t_n, extrapolation ratio rho of the source signal, squared tolerance
+enum StepSlot { ST_T = 0, ST_RHO, ST_TOL2, ST_N = 4 };
 enum RedOp { OP_STORE = 0, OP_PQ = 1, OP_RZ_INIT = 2, OP_RZ = 3, OP_RNORM = 4, OP_RNORM0 = 5 };
 constexpr int RED_BLOCKS = 296;  // fixed grid of the two-stage reductions (deterministic)
 

@@ -73,6 +73,8 @@ __device__ void apply_op(int op, double v, double *sc, int *fl) {
       break;
     case OP_RNORM0:
       sc[SC_RNORM2] = v;
+      sc[SC_RMIN] = v;
+      fl[FL_STAG] = 0;
       if (!isfinite(v)) { fl[FL_STATUS] = DS_NONFINITE; fl[FL_DONE] = 1; }
       else if (v <= sc[SC_TOL2] * sc[SC_REF2]) fl[FL_DONE] = 1;
       break;
@@ -82,6 +84,13 @@ __device__ void apply_op(int op, double v, double *sc, int *fl) {
       if (!isfinite(v)) { fl[FL_STATUS] = DS_NONFINITE; fl[FL_DONE] = 1; }
       else if (v <= sc[SC_TOL2] * sc[SC_REF2]) fl[FL_DONE] = 1;
       else if (fl[FL_ITER] >= fl[FL_MAXIT]) fl[FL_DONE] = 1;
+      else if (v < 0.25 * sc[SC_RMIN]) { sc[SC_RMIN] = v; fl[FL_STAG] = 0; }
+      else if (fl[FL_STAGWIN] > 0 && ++fl[FL_STAG] >= fl[FL_STAGWIN]) {
+        // stagnation (the inexact FP32 operator of the loop can stall the recursion): stop
+        // this round; the true-residual check restarts from the true residual
+        fl[FL_DONE] = 1;
+        fl[FL_NSTAG] += 1;
+      }
       break;
   }
 }
@@ -232,38 +241,51 @@ __global__ void k_bnd_apply(DevTopo D, const double *csr_val, const double *y, d
 }
 
 // ------------------------------ iterative refinement ---------------------------------
-// r = b - K_N x in FP64 from the assembled CSR values, K_N being K_s with identity rows and
-// columns on the fixed dofs of floating subdomains (the matrix whose factor gives K^+).
-// One CTA per subdomain, one warp per row, fixed-order sums.
-__global__ void k_residual_N(DevTopo D, const double *csr_val, const double *b, const double *x, double *r,
-                             const int *skip) {
+// Sliced-ELL values of every subdomain from its assembled CSR values (sell_src: CSR entry,
+// -1 padding, -2 the unit diagonal of a fixed row).
+__global__ void k_csr_to_sell(DevTopo D, const double *__restrict__ csr_val, double *__restrict__ sell_val) {
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int *src = D.pool + t.sell_src;
+  const double *cv = csr_val + D.csr_off[s];
+  double *sv = sell_val + D.sell_off[s];
+  const long long nslot = D.sell_off[s + 1] - D.sell_off[s];
+  for (long long i = threadIdx.x; i < nslot; i += blockDim.x) {
+    const int e = src[i];
+    sv[i] = e >= 0 ? cv[e] : (e == -2 ? 1.0 : 0.0);
+  }
+}
+
+// FP64 residual r = b - K_N x of the refinement sweeps (mixed precision), K_N the Neumann
+// matrix with the generalised-inverse convention (fixed rows and columns replaced by the
+// identity).  One CTA per subdomain, one thread per row over the sliced ELL copy, so every
+// warp load of values and column indices is one contiguous segment; a row's entries are
+// summed in column order.
+__global__ void k_residual_N(DevTopo D, const double *__restrict__ sell_val, const double *__restrict__ b,
+                             const double *__restrict__ x, double *__restrict__ r, const int *skip) {
   if (skip && *skip) return;
   const int s = blockIdx.x;
   const DevTpl t = D.tpl[D.sub_tpl[s]];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long off = D.vec_off[s];
-  const int *cptr = D.pool + t.csr_ptr, *ccol = D.pool + t.csr_col;
-  const double *val = csr_val + D.csr_off[s];
-  auto fixed = [&](int d) { return t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2); };
-  for (int row = warp; row < t.n; row += nw) {
-    if (fixed(row)) {
-      if (lane == 0) r[off + row] = b[off + row] - x[off + row];
-      continue;
-    }
+  const int *sptr = D.pool + t.sell_ptr, *scol = D.pool + t.sell_col;
+  const double *val = sell_val + D.sell_off[s];
+  const double *xs = x + off;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = warp; q < t.nslice; q += nw) {
+    const int row = 32 * q + lane;
+    const int p1 = sptr[q + 1];
     double acc = 0.0;
-    for (int e = cptr[row] + lane; e < cptr[row + 1]; e += 32) {
-      const int c = ccol[e];
-      if (!fixed(c)) acc += val[e] * x[off + c];
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) r[off + row] = b[off + row] - acc;
+    for (int p = sptr[q] + lane; p < p1; p += 32) acc += val[p] * xs[scol[p]];
+    if (row < t.n) r[off + row] = b[off + row] - acc;
   }
 }
 
 // Refinement stop test: after x += r, skip further sweeps once ||r|| <= eps ||x|| (2-norms
-// over all subdomains).  Counts performed sweeps in fl[FL_IRSWEEPS].
+// over all subdomains), or, with stag2 > 0, once the correction stagnates: ||r||^2 >
+// stag2 ||r_prev||^2 means the sweeps have reached the rounding floor of the FP64 residual.
+// prev2 holds ||r_prev||^2 (0 before the first sweep).  Counts sweeps in fl[FL_IRSWEEPS].
 __global__ void k_ir_check(const double *x, const double *r, long long n, double eps2, double *partial,
-                           unsigned *counter, int *fl) {
+                           unsigned *counter, int *fl, double *prev2, double stag2) {
   if (fl[FL_IRSKIP]) return;
   double sr = 0.0, sx = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -279,7 +301,9 @@ __global__ void k_ir_check(const double *x, const double *r, long long n, double
     double t1 = 0.0;
     for (int i = 0; i < (int)gridDim.x; ++i) t1 += ((volatile double *)partial)[i];
     fl[FL_IRSWEEPS] += 1;
-    if (t1 <= eps2 * tx || !(t1 == t1)) fl[FL_IRSKIP] = 1;
+    if (t1 <= eps2 * tx || !(t1 == t1) || (stag2 > 0.0 && *prev2 > 0.0 && t1 > stag2 * *prev2))
+      fl[FL_IRSKIP] = 1;
+    *prev2 = t1;
   }
 }
 
@@ -339,8 +363,9 @@ __global__ void k_Gcomb(DevTopo D, const double *alpha, const double *v, double 
 // (Eq. (2.42) with eta eliminated).  Writes f into xf (fixed dofs of floating subdomains
 // zeroed, the K^+ convention) and e_f = R_f^T f_f for floating subdomains.
 __global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double *Zn, const double *E0n,
-                      const double *Reta, double t_now, double *xf, double *e) {
+                      const double *Reta, const double *stepv, double *xf, double *e) {
   const int s = blockIdx.x;
+  const double t_now = stepv[ST_T];
   const DevTpl t = D.tpl[D.sub_tpl[s]];
   const double *fs = fstat + D.vec_off[s];
   double *x = xf + D.vec_off[s];
@@ -463,6 +488,48 @@ __global__ void k_identity(double *X, int nH) {
   const long long tot = (long long)nH * nH;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
     X[e] = (e / nH == e % nH) ? 1.0 : 0.0;
+}
+
+// ------------------------- loop control of the per-step graph -------------------------
+// The Krylov loop of a time step runs as two nested conditional WHILE nodes: the outer one
+// restarts from the true residual, the inner one runs chunks of PCG iterations.  These
+// single-thread kernels set the loop conditions from the device flags; every loop is also
+// bounded by a count (restarts, bodies), so the graph ends whatever the flags say.
+__global__ void k_loop_arm_outer(cudaGraphConditionalHandle hc, int *fl) {
+  fl[FL_RESTARTS] = 0;
+  fl[FL_PENDING] = 0;
+  cudaGraphSetConditional(hc, 1u);
+}
+
+__global__ void k_loop_arm_inner(cudaGraphConditionalHandle hc, int *fl) {
+  fl[FL_BODY] = 0;
+  cudaGraphSetConditional(hc, fl[FL_DONE] ? 0u : 1u);
+}
+
+__global__ void k_loop_inner(cudaGraphConditionalHandle hc, int *fl, int max_body) {
+  const int b = ++fl[FL_BODY];
+  const bool more = !fl[FL_DONE] && fl[FL_ITER] < fl[FL_MAXIT] && b < max_body;
+  cudaGraphSetConditional(hc, more ? 1u : 0u);
+}
+
+// after the true residual ||P(d - F lambda)||^2 has been stored in SC_TRUE2: restart while it
+// misses the tolerance, no breakdown was flagged and the restart and iteration budgets last
+__global__ void k_loop_outer(cudaGraphConditionalHandle hc, int *fl, const double *sc, int max_restarts) {
+  const bool ok = sc[SC_TRUE2] <= sc[SC_TOL2] * sc[SC_REF2];
+  const bool again = !ok && !fl[FL_STATUS] && fl[FL_RESTARTS] < max_restarts && fl[FL_ITER] < fl[FL_MAXIT];
+  if (again) {
+    fl[FL_RESTARTS] += 1;
+    fl[FL_DONE] = 0;
+  }
+  fl[FL_PENDING] = again ? 1 : 0;
+  cudaGraphSetConditional(hc, again ? 1u : 0u);
+}
+
+// dst = src when *flag is set (the restart's r = true residual)
+__global__ void k_copy_if(double *dst, const double *src, long long n, const int *flag) {
+  if (!*flag) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
 }
 
 }  // namespace fp

@@ -39,6 +39,10 @@ struct Template {
   // halo rows: rows not in bnd with at least one column in bnd; entries = csr indices
   std::vector<int> halo_ptr, halo_row, halo_ent;
   std::vector<int> elem_dofs;            // [n_elem * ndl] element dof lists (-1 Dirichlet)
+  // sliced ELL copy of the Neumann matrix with the generalised-inverse convention (entries in
+  // fixed columns dropped, unit diagonal on fixed rows): slices of 32 rows, entry k of row
+  // 32 q + l at slot sell_ptr[q] + 32 k + l; sell_src = CSR entry index, -1 padding, -2 unit
+  std::vector<int> sell_ptr, sell_col, sell_src;
   int ndl;                               // local dofs per element
 };
 
@@ -55,6 +59,7 @@ struct Topology {
   std::vector<long long> csr_off;        // [S+1] offsets of CSR value arrays
   std::vector<long long> unode_off, pnode_off;  // [S+1] canonical field offsets
   std::vector<long long> elem_off;       // [S+1] element offsets (perm)
+  std::vector<long long> sell_off;       // [S+1] offsets of sliced-ELL value arrays
   // interface
   int n_lambda = 0, n_lambda_p = 0;
   std::vector<int> lam_key;              // [6 * n_lambda]

@@ -235,9 +235,10 @@ __global__ void k_mlp_init(float *P, unsigned long long seed) {
 // dl = l1 - l2 (features are free of the node position, so nothing ties the network to the
 // source location it was trained on),
 // s1 = RMS(dl), s0 = RMS(l1) (from the sums of squares in sums[0], sums[1]).
-__global__ void k_features(int n, const double *l1, const double *l2, const double *sums, double rho,
+__global__ void k_features(int n, const double *l1, const double *l2, const double *sums, const double *stepv,
                            const float *xy, const int *kind, const int *comp, float *X, float *scale_out) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const double rho = stepv[ST_RHO];
   const double s1 = sqrt(sums[0] / n) + 1e-300, s0 = sqrt(sums[1] / n) + 1e-300;
   if (r == 0 && scale_out) scale_out[0] = (float)s1;
   if (r >= n) return;

@@ -175,6 +175,35 @@ void build_template(Template &t) {
     t.fixed[1] = t.udof[1];
     t.fixed[2] = t.udof[2 * (t.nux - 1) + 1];
   }
+  // sliced ELL (32-row slices, column-major inside a slice) of the Neumann matrix
+  auto is_fixed = [&](int d) { return t.floating && (d == t.fixed[0] || d == t.fixed[1] || d == t.fixed[2]); };
+  const int nslice = (n + 31) / 32;
+  t.sell_ptr.assign(nslice + 1, 0);
+  t.sell_col.clear();
+  t.sell_src.clear();
+  for (int q = 0; q < nslice; ++q) {
+    std::vector<std::vector<std::pair<int, int>>> ent(32);  // (col, src) per row of the slice
+    int w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int r = 32 * q + l;
+      if (r >= n) continue;
+      if (is_fixed(r)) {
+        ent[l].push_back({r, -2});
+      } else {
+        for (int e = t.csr_ptr[r]; e < t.csr_ptr[r + 1]; ++e)
+          if (!is_fixed(t.csr_col[e])) ent[l].push_back({t.csr_col[e], e});
+      }
+      w = std::max(w, (int)ent[l].size());
+    }
+    for (int k2 = 0; k2 < w; ++k2)
+      for (int l = 0; l < 32; ++l) {
+        const int r = std::min(32 * q + l, n - 1);
+        const bool real = k2 < (int)ent[l].size();
+        t.sell_col.push_back(real ? ent[l][k2].first : r);
+        t.sell_src.push_back(real ? ent[l][k2].second : -1);
+      }
+    t.sell_ptr[q + 1] = (int)t.sell_col.size();
+  }
 }
 
 struct NodeEnt { int s, d0, d1; };
@@ -240,6 +269,7 @@ bool build_topology(const fp_mesh_desc *m, const fp_params *p, Topology &T, std:
   // offsets
   T.vec_off.assign(S + 1, 0); T.fac_off.assign(S + 1, 0); T.csr_off.assign(S + 1, 0);
   T.unode_off.assign(S + 1, 0); T.pnode_off.assign(S + 1, 0); T.elem_off.assign(S + 1, 0);
+  T.sell_off.assign(S + 1, 0);
   for (int s = 0; s < S; ++s) {
     const Template &t = T.tpl[T.sub_tpl[s]];
     T.vec_off[s + 1] = T.vec_off[s] + round_up(t.n, 32);
@@ -248,6 +278,7 @@ bool build_topology(const fp_mesh_desc *m, const fp_params *p, Topology &T, std:
     T.unode_off[s + 1] = T.unode_off[s] + (long long)t.nux * t.nuy;
     T.pnode_off[s + 1] = T.pnode_off[s] + (long long)t.npx * t.npy;
     T.elem_off[s + 1] = T.elem_off[s] + 2LL * t.nx * t.ny;
+    T.sell_off[s + 1] = T.sell_off[s] + (long long)t.sell_col.size();
   }
   // ---- interface constraints (signed Boolean jump operator, non-redundant chains) ----
   std::map<std::pair<int, int>, std::vector<NodeEnt>> umap, pmap;  // key (J, I) for sorting

@@ -22,6 +22,7 @@ FP_OK = 0
 STATUS_NAMES = {0: "FP_OK", 1: "FP_ERR_INVALID", 2: "FP_ERR_OOM", 3: "FP_ERR_CUDA",
                 4: "FP_ERR_NOT_CONVERGED", 5: "FP_ERR_BREAKDOWN", 6: "FP_ERR_TIMEOUT",
                 7: "FP_ERR_STATE"}
+globals().update({name: code for code, name in STATUS_NAMES.items()})
 FP_SOURCE_MANUFACTURED, FP_SOURCE_POINT, FP_SOURCE_MANUFACTURED_T = 0, 1, 2
 FP_PREC_FP64, FP_PREC_MIXED = 0, 1
 FP_PRECOND_DIRICHLET, FP_PRECOND_NONE = 0, 2
@@ -31,7 +32,7 @@ EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_ge
             "fp_apply_precond", "fp_apply_projection", "fp_apply_projection_noalloc",
             "fp_get_dof_map",
             "fp_get_local_matrix", "fp_get_step_timing", "fp_set_option", "fp_set_profiling",
-            "fp_get_kernel_stats", "fp_learned_record", "fp_learned_use", "fp_learned_train",
+            "fp_get_kernel_stats", "fp_get_tuning", "fp_learned_record", "fp_learned_use", "fp_learned_train",
             "fp_learned_num_samples", "fp_mlp_init", "fp_mlp_set_params", "fp_mlp_get_params",
             "fp_mlp_forward", "fp_mlp_loss_grad", "fp_last_error", "fp_destroy"]
 MLP_NPARAM = 8 * 256 + 256 + 256 * 256 + 256 + 256 + 1
@@ -65,11 +66,18 @@ class KernelStats(ctypes.Structure):
                 ("bytes_per_launch", ctypes.c_double), ("flops_per_launch", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("factor_nb", ctypes.c_int), ("solve_wpc", ctypes.c_int), ("solve_chunk", ctypes.c_int),
+                ("solve_ctas_per_sm", ctypes.c_int), ("factor_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
 class StepStats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("iterations", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
                 ("lambda0_learned", ctypes.c_int), ("guess_res_prev", ctypes.c_double),
-                ("guess_res_learned", ctypes.c_double)]
+                ("guess_res_learned", ctypes.c_double), ("restarts", ctypes.c_int),
+                ("stagnations", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -91,6 +99,7 @@ _lib.fp_get_step_timing.argtypes = [_vp, _vp]
 _lib.fp_set_option.argtypes = [_vp, ctypes.c_char_p, ctypes.c_double]
 _lib.fp_set_profiling.argtypes = [_vp, ctypes.c_int]
 _lib.fp_get_kernel_stats.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(KernelStats)]
+_lib.fp_get_tuning.argtypes = [_vp, ctypes.POINTER(Tuning)]
 _lib.fp_learned_record.argtypes = [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_int]
 _lib.fp_learned_use.argtypes = [_vp, ctypes.c_int]
 _lib.fp_learned_train.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong,
@@ -182,7 +191,8 @@ class Solver:
         return {"status": rc, "step": st.step, "iterations": st.iterations,
                 "rel_residual": st.rel_residual, "true_rel_residual": st.true_rel_residual,
                 "lambda0_learned": st.lambda0_learned, "guess_res_prev": st.guess_res_prev,
-                "guess_res_learned": st.guess_res_learned}
+                "guess_res_learned": st.guess_res_learned, "restarts": st.restarts,
+                "stagnations": st.stagnations}
 
     def run(self, n_steps):
         st = StepStats()
@@ -295,6 +305,11 @@ class Solver:
 
     def set_profiling(self, on=True):
         self._check(_lib.fp_set_profiling(self._h, 1 if on else 0))
+
+    def tuning(self):
+        t = Tuning()
+        self._check(_lib.fp_get_tuning(self._h, ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def kernel_stats(self, kind):
         s = KernelStats()
