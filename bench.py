@@ -112,7 +112,8 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate of the profiling recipe's tab
 # record holds only while the kernel source and its launch shape are the ones captured.
 TRAFFIC_RECORDS = [
     {"workload": "config5", "precision": "mixed", "kernel": "k_band_solve_blk<float>",
-     "shape": None, "band_cu_sha256": None, "bytes_per_launch": None},
+     "shape": [8, 4096, 2], "band_cu_sha256": "14f2dc3e7b85ed1cfc01ae558464fa0c1bc73c0fc89f173be89354b81be1ae27",
+     "bytes_per_launch": 54.394e9 + 0.378e9},
 ]
 
 
@@ -194,7 +195,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     sol = F.Solver(case, stream=stream.cuda_stream)
     for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
-                     ("factor_fp64", args.factor_fp64), ("graph", args.graph)):
+                     ("factor_fp64", args.factor_fp64), ("graph", args.graph), ("factor_nb", args.factor_nb)):
         if val is not None:
             sol.set_option(key, val)
     t0 = time.perf_counter()
@@ -234,13 +235,14 @@ def run_native(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     torch.cuda.nvtx.range_push("timed_region")  # lets ncu select the timed launches
-    its, restarts, wins, stags = [], [], [], []
+    its, restarts, wins, stags, gres = [], [], [], [], []
     for _ in range(args.steps):
         st = sol.step()
         its.append(st["iterations"])
         wins.append(st["lambda0_learned"])
         restarts.append(st["restarts"])
         stags.append(st["stagnations"])
+        gres.append([st["guess_res_prev"], st["guess_res_learned"]])
     torch.cuda.nvtx.range_pop()
     ev1.record(stream)
     barrier()
@@ -308,6 +310,7 @@ def run_native(args):
                        "pcg_stagnation_stops": stags, "autotuned": tuning,
                        "graph": args.graph != 0, "learned_lambda0": learned,
                        "learned_guess_chosen": wins if learned else None,
+                       "guess_rel_residual_prev_learned": gres if learned else None,
                        "learned_record_steps": args.learned_record_steps if learned else 0,
                        "learned_record_s": record_s, "learned_train_s": train_s,
                        "learned_train_loss": train_loss,
@@ -367,6 +370,7 @@ def main():
     ap.add_argument("--wpc", type=int, default=None, help="warps per CTA of the local solves")
     ap.add_argument("--chunk", type=int, default=None, help="bytes per shared-memory stage of the solves")
     ap.add_argument("--factor-fp64", type=int, default=None, help="mixed: factor in FP64, round to FP32")
+    ap.add_argument("--factor-nb", type=int, default=None, help="panel width of the factorisation")
     ap.add_argument("--graph", type=int, default=None, help="1: one CUDA graph launch per time step")
     ap.add_argument("--learned", type=int, default=1, help="mixed arm: learned lambda_0 (trained in warm-up)")
     ap.add_argument("--learned-epochs", type=int, default=8)
