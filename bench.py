@@ -195,7 +195,8 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     sol = F.Solver(case, stream=stream.cuda_stream)
     for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
-                     ("factor_fp64", args.factor_fp64), ("graph", args.graph), ("factor_nb", args.factor_nb)):
+                     ("factor_fp64", args.factor_fp64), ("graph", args.graph), ("factor_nb", args.factor_nb),
+                     ("explicit", args.explicit)):
         if val is not None:
             sol.set_option(key, val)
     t0 = time.perf_counter()
@@ -308,7 +309,8 @@ def run_native(args):
                        "factor_gb": s.factor_bytes / 1e9, "l2": "inputs larger than L2 (factors %.1f GB)"
                        % (s.factor_bytes / 1e9), "setup_s": setup_s, "pcg_iterations": its, "pcg_restarts": restarts,
                        "pcg_stagnation_stops": stags, "autotuned": tuning,
-                       "graph": args.graph != 0, "learned_lambda0": learned,
+                       "graph": args.graph != 0, "explicit_operators": bool(args.explicit),
+                       "learned_lambda0": learned,
                        "learned_guess_chosen": wins if learned else None,
                        "guess_rel_residual_prev_learned": gres if learned else None,
                        "learned_record_steps": args.learned_record_steps if learned else 0,
@@ -332,8 +334,12 @@ def run_native(args):
         # the comparison arm of the metric: plain FP64 FETI on the same workload
         c64 = case.with_(precision="fp64")
         s64 = F.Solver(c64, stream=stream.cuda_stream)
+        if args.fp64_explicit is not None:
+            s64.set_option("explicit", args.fp64_explicit)
+        t0 = time.perf_counter()
         s64.assemble()
         s64.factor()
+        setup64 = time.perf_counter() - t0
         for _ in range(args.warmup):
             s64.step()
         barrier()
@@ -345,7 +351,8 @@ def run_native(args):
         ms64 = e0.elapsed_time(e1)
         line["fp64_arm"] = {"value": world * args.fp64_steps / (ms64 / 1000.0), "unit": "steps/s",
                             "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps,
-                            "pcg_iterations": its64,
+                            "pcg_iterations": its64, "setup_s": setup64, "autotuned": s64.tuning(),
+                            "explicit_operators": bool(args.fp64_explicit),
                             "speedup_of_value": value / (world * args.fp64_steps / (ms64 / 1000.0))}
         s64.close()
     if rank == 0:
@@ -371,6 +378,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=None, help="bytes per shared-memory stage of the solves")
     ap.add_argument("--factor-fp64", type=int, default=None, help="mixed: factor in FP64, round to FP32")
     ap.add_argument("--factor-nb", type=int, default=None, help="panel width of the factorisation")
+    ap.add_argument("--explicit", type=int, default=1, help="1: explicit local interface operators")
+    ap.add_argument("--fp64-explicit", type=int, default=1, help="explicit operators in the FP64 arm")
     ap.add_argument("--graph", type=int, default=None, help="1: one CUDA graph launch per time step")
     ap.add_argument("--learned", type=int, default=1, help="mixed arm: learned lambda_0 (trained in warm-up)")
     ap.add_argument("--learned-epochs", type=int, default=8)

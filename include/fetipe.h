@@ -251,6 +251,20 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *   "solve_cps"    [0]  CTAs per SM of the blocked solves, 1..2 (0: autotuned, or 1)
  *   "factor_nb"    [0]  panel width of the factorisation, 4..64, multiple of 4 (0: autotuned,
  *                       or the widest of 32, 16, 8, 4 whose panel fits in shared memory)
+ *   "explicit"     [0]  1: fp_factor also forms the local interface operators explicitly,
+ *                       F_s = (K_s^+) restricted to the dofs touched by B_s and the Dirichlet
+ *                       Schur complement S_s (dense m_s x m_s per subdomain, the factors'
+ *                       precision; m_s = 480 for a 24 x 24-cell P2 poroelastic subdomain with
+ *                       four interface sides), by multi-right-hand-side
+ *                       band solves; F and the Dirichlet preconditioner are then applied as
+ *                       batched dense products.  FP64: F_s, S_s in FP64 for every apply.
+ *                       Mixed: F_s is formed in FP64 from the FP64 factorisation (with
+ *                       "factor_fp64", the default) and serves every accurate apply, its FP32
+ *                       rounding serves the PCG loop; S_s is FP32 from the FP32 factors (without
+ *                       "factor_fp64": F_s FP32 for the loop only, accurate applies keep the
+ *                       refined band solves).  The right-hand side and the recovery keep full
+ *                       band solves.  Needs b + 64 window rows of 32 values in shared memory
+ *                       (FP_ERR_INVALID when the band is too wide).  Takes effect at fp_factor.
  *   "autotune"     [1]  fp_factor times candidate launch shapes on the handle's own factors
  *                       and keeps the fastest (see fp_get_tuning); explicitly set shape
  *                       options are kept fixed.  Takes effect at the next fp_factor.
@@ -299,6 +313,7 @@ typedef struct {
   int solve_wpc, solve_chunk, solve_ctas_per_sm;
   double factor_ms, solve_ms;
   int candidates;
+  double explicit_ms;  /* build time of the explicit interface operators (0: not built) */
 } fp_tuning;
 fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out);
 

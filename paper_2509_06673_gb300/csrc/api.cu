@@ -28,6 +28,14 @@ cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int ch
 cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
                              cudaStream_t stream);
 cudaError_t launch_round_to_float(const double *src, float *dst, long long n, cudaStream_t stream);
+size_t mrhs_smem_bytes(bool fp32, int R, int LDp);
+cudaError_t launch_band_mrhs(bool fp32, int nr, int grid, cudaStream_t st, const int *task_s, const int *task_j0,
+                             int ntask, DevTopo D, const void *fac, const void *linv, const long long *linv_off,
+                             const double *csr, int kind, void *scratch, long long sstride, int *counter, void *out,
+                             const long long *out_off, int R, int LDp);
+int mrhs_blocks_per_sm(bool fp32, int nr, int R, int LDp);
+cudaError_t launch_explicit_apply(bool fp32, DevTopo D, int S, int mmax_bnd, const void *ops, const long long *op_off,
+                                  double *xloc, const int *fl, cudaStream_t st);
 __global__ void k_dot(const double *, const double *, long long, double *, unsigned *, double *, int *, int,
                       double *, int);
 __global__ void k_pcg_update(double *, double *, const double *, const double *, long long, double *, unsigned *,
@@ -115,6 +123,15 @@ struct fp_handle {
   struct SolveShape { int wpc, chunk, cps; };
   SolveShape shape{0, 0, 0};  // launch shape of the blocked solves (set at fp_factor)
   fp_tuning tuning{};
+  // explicit local interface operators F_s, S_s (dense, per subdomain; option "explicit")
+  int explicit_ops = 0, ops_ready = 0, opF64_ready = 0;
+  void *opF = nullptr, *opS = nullptr;  // the PCG loop's operators (factor precision)
+  double *opF64 = nullptr;              // mixed precision: F_s in FP64 for the accurate applies
+  const long long *op_off = nullptr, *linv_off_dev = nullptr;
+  long long op_total = 0;
+  const int *mrhs_s = nullptr, *mrhs_j0 = nullptr;
+  int mrhs_ntask = 0;
+  double explicit_build_ms = 0;
   int factor_fp64 = 1;     // mixed precision: factor in FP64, round the finished factor to FP32
   double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
   BandTask *tasksN = nullptr, *tasksD = nullptr, *taskH = nullptr, *tasksHinv = nullptr;
@@ -313,6 +330,26 @@ fp_status build_device(fp_handle *h) {
   std::vector<long long> linv_off(T.S + 1, 0);
   for (int s = 0; s < T.S; ++s) linv_off[s + 1] = linv_off[s] + 1024LL * ((T.tpl[T.sub_tpl[s]].n + 31) / 32);
   h->linv_total = linv_off[T.S];
+  TRY(upload(h, &h->linv_off_dev, linv_off));
+  {
+    // explicit-operator layout (rows padded to a multiple of 4) and build tasks: every
+    // subdomain in cost order, tiles of 32 right-hand sides
+    std::vector<long long> ooff(T.S + 1, 0);
+    std::vector<int> ms, mj;
+    for (int s = 0; s < T.S; ++s) {
+      const long long m = (long long)T.tpl[T.sub_tpl[s]].bnd.size();
+      ooff[s + 1] = ooff[s] + m * ((m + 3) & ~3LL);
+    }
+    for (int s : order) {
+      const int m = (int)T.tpl[T.sub_tpl[s]].bnd.size();
+      for (int j0 = 0; j0 < m; j0 += 32) { ms.push_back(s); mj.push_back(j0); }
+    }
+    h->op_total = ooff[T.S];
+    h->mrhs_ntask = (int)ms.size();
+    TRY(upload(h, &h->op_off, ooff));
+    TRY(upload(h, &h->mrhs_s, ms));
+    TRY(upload(h, &h->mrhs_j0, mj));
+  }
   std::vector<BandTask> tk;
   int mmax = 1;
   for (int s : order) {
@@ -574,6 +611,17 @@ double *xsol(fp_handle *h) { return h->P.precision == FP_PREC_MIXED ? h->XA : h-
 fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, bool accurate = true) {
   k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, v, 1.0, h->XB, 1, fl);
   CKL();
+  // explicit F_s: every apply in FP64, the loop's inexact apply in mixed precision (only the
+  // rows touched by B are formed, so K^+ B^T v is not left in xsol)
+  const bool mixed = h->P.precision == FP_PREC_MIXED;
+  const void *op = nullptr;
+  if (h->ops_ready) op = !mixed || !accurate ? h->opF : (h->opF64_ready ? h->opF64 : nullptr);
+  if (op) {
+    CK(launch_explicit_apply(mixed && !accurate, h->D, h->T.S, h->nbnd_max, op, h->op_off, h->XB, fl, h->stream));
+    k_gather<<<(h->T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->XB, out, fl);
+    CKL();
+    return FP_OK;
+  }
   double *x = h->XB;
   if (h->P.precision == FP_PREC_MIXED) {
     x = h->XA;
@@ -596,10 +644,16 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
   }
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
   k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl);
-  k_halo<<<h->T.S, 256, 0, h->stream>>>(h->D, h->csr_val, h->XP, h->XY, fl);
   CKL();
-  TRY(solve_local(h, true, h->XY, fl));
-  k_bnd_apply<<<h->T.S, 256, h->nbnd_max * sizeof(double), h->stream>>>(h->D, h->csr_val, h->XY, h->XP, fl);
+  if (h->ops_ready) {
+    CK(launch_explicit_apply(h->P.precision == FP_PREC_MIXED, h->D, h->T.S, h->nbnd_max, h->opS, h->op_off, h->XP,
+                             fl, h->stream));
+  } else {
+    k_halo<<<h->T.S, 256, 0, h->stream>>>(h->D, h->csr_val, h->XP, h->XY, fl);
+    CKL();
+    TRY(solve_local(h, true, h->XY, fl));
+    k_bnd_apply<<<h->T.S, 256, h->nbnd_max * sizeof(double), h->stream>>>(h->D, h->csr_val, h->XY, h->XP, fl);
+  }
   k_gather<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, h->t2, fl);
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, h->t2, out, fl);
   CKL();
@@ -694,6 +748,8 @@ fp_status build_features(fp_handle *h) {
 }
 
 fp_status choose_nb(fp_handle *h, bool dbl, const BandTask *tasks, void *buf, int *nb_out);
+fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, int kind, void *out);
+fp_status alloc_op(fp_handle *h, void **p, size_t esz);
 
 template <typename T>
 fp_status factor_T(fp_handle *h) {
@@ -731,6 +787,18 @@ fp_status factor_T(fp_handle *h) {
       if (ee == cudaSuccess) ee = launch_round_to_float(tN, (float *)dstF, (long long)nf, h->stream);
       if (ee == cudaSuccess) ee = launch_round_to_float(tL, (float *)dstL, h->linv_total, h->stream);
       if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
+      if (st == FP_OK && mode == 0 && h->explicit_ops) {
+        // F_s in FP64 from the FP64 factor (the accurate applies), and its FP32 rounding (the
+        // PCG loop's operator)
+        st = alloc_op(h, (void **)&h->opF64, 8);
+        if (st == FP_OK) st = alloc_op(h, &h->opF, 4);
+        if (st == FP_OK) st = run_mrhs(h, false, tN, tL, 0, h->opF64);
+        if (st == FP_OK) {
+          ee = launch_round_to_float(h->opF64, (float *)h->opF, h->op_total, h->stream);
+          if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
+        }
+        if (st == FP_OK) h->opF64_ready = 1;
+      }
     }
     cudaStreamSynchronize(h->stream);
     cudaFree(tN);
@@ -855,6 +923,63 @@ fp_status autotune_solve(fp_handle *h) {
   h->tuning.solve_wpc = h->shape.wpc;
   h->tuning.solve_chunk = h->shape.chunk;
   h->tuning.solve_ctas_per_sm = h->shape.cps;
+  return FP_OK;
+}
+
+// ---------------------------- explicit interface operators ------------------------------
+// One operator for every subdomain by the multi-right-hand-side band kernel: kind 0 F_s =
+// (K_s^+)_{bb} from Neumann factors, kind 1 S_s = K_bb - K_bi K_ii^{-1} K_ib from Dirichlet
+// factors, in the precision of the factors given (fp32).  out: op_total entries.
+fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, int kind, void *out) {
+  const size_t esz = fp32 ? 4 : 8;
+  int bmax = 0, nmax = 0;
+  for (const Template &t : h->T.tpl) { bmax = std::max(bmax, t.b); nmax = std::max(nmax, t.n); }
+  const int R = (bmax + 64 + 31) / 32 * 32, LDp = h->ldmax + 4, nr = (bmax + 31) / 32;
+  if (nr > 16 || mrhs_smem_bytes(fp32, R, LDp) > 227 * 1024) {
+    h->err = "explicit operators: the band is too wide for the shared-memory window";
+    return FP_ERR_INVALID;
+  }
+  const int bps = mrhs_blocks_per_sm(fp32, nr, R, LDp);
+  if (bps < 1) { h->err = "explicit operators: build kernel cannot be resident"; return FP_ERR_CUDA; }
+  const int grid = std::min(bps * h->num_sms, std::max(1, h->mrhs_ntask));
+  CK(cudaMemsetAsync(out, 0, (size_t)h->op_total * esz, h->stream));
+  const long long sstride = (long long)nmax * 32;
+  void *scratch = nullptr;
+  CK(cudaMalloc(&scratch, (size_t)grid * sstride * esz));
+  CK(cudaEventRecord(h->ev[4], h->stream));
+  cudaError_t e = cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess)
+    e = launch_band_mrhs(fp32, nr, grid, h->stream, h->mrhs_s, h->mrhs_j0, h->mrhs_ntask, h->D, fac, linv,
+                         h->linv_off_dev, h->csr_val, kind, scratch, sstride, h->counter, out, h->op_off, R, LDp);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev[5], h->stream);
+  const cudaError_t es = cudaStreamSynchronize(h->stream);
+  cudaFree(scratch);
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) { h->err = std::string("explicit operators: ") + cudaGetErrorString(e); return FP_ERR_CUDA; }
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]);
+  h->tuning.explicit_ms += ms;
+  return FP_OK;
+}
+
+fp_status alloc_op(fp_handle *h, void **p, size_t esz) {
+  if (!*p) {
+    CK(cudaMalloc(p, (size_t)h->op_total * esz));
+    h->allocs.push_back(*p);
+  }
+  return FP_OK;
+}
+
+// FP64: F_s and S_s in FP64.  Mixed: S_s in FP32 from the FP32 Dirichlet factors; F_s in FP32
+// unless the factorisation already formed it in FP64 (then opF is that, rounded once).
+fp_status build_explicit(fp_handle *h) {
+  const bool fp32 = h->P.precision == FP_PREC_MIXED;
+  const size_t esz = fp32 ? 4 : 8;
+  TRY(alloc_op(h, &h->opF, esz));
+  TRY(alloc_op(h, &h->opS, esz));
+  if (!h->opF64_ready) TRY(run_mrhs(h, fp32, h->facN, h->linvN, 0, h->opF));
+  TRY(run_mrhs(h, fp32, h->facD, h->linvD, 1, h->opS));
+  h->ops_ready = 1;
   return FP_OK;
 }
 
@@ -1107,6 +1232,14 @@ fp_status step_recovery(fp_handle *h) {
     k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->cy, h->calpha, T.nH, nullptr);
     CKL();
   }
+  if (h->ops_ready && (h->P.precision == FP_PREC_FP64 || h->opF64_ready)) {
+    // the explicit accurate apply formed only the interface rows of K^+ B^T lambda: one full
+    // (refined) solve for the recovery
+    k_scatter<<<T.S, 256, 0, s>>>(h->D, h->lam, 1.0, h->XB, 1, nullptr);
+    CKL();
+    if (h->P.precision == FP_PREC_MIXED) TRY(solve_refined(h, h->XB, h->XA, h->ir_sweeps, nullptr));
+    else TRY(solve_local(h, false, h->XB, nullptr));
+  }
   k_recover<<<T.S, 256, 0, s>>>(h->D, h->DP, h->X2, xsol(h), h->calpha, h->U, h->XI, h->ETA, h->PP, h->Reta);
   CKL();
   return FP_OK;
@@ -1248,11 +1381,18 @@ fp_status fp_factor(fp_handle *h) {
   if (!h) return FP_ERR_INVALID;
   if (h->stage < 1) { h->err = "fp_factor before fp_assemble"; return FP_ERR_STATE; }
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  h->ops_ready = 0;
+  h->opF64_ready = 0;
+  h->tuning.explicit_ms = 0;
   TRY(h->P.precision == FP_PREC_MIXED ? factor_T<float>(h) : factor_T<double>(h));
   TRY(factor_coarse(h));
   TRY(check_status(h));
   TRY(autotune_solve(h));
   TRY(check_status(h));
+  if (h->explicit_ops) {
+    TRY(build_explicit(h));
+    TRY(check_status(h));
+  }
   h->stage = 2;
   h->gdirty = 1;
   return FP_OK;
@@ -1609,6 +1749,7 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "solve_chunk") { if (v != 0 && (v < 4096 || v > 65536 || v % 1024)) return bad(); h->solve_chunk = v; }
   else if (k == "solve_cps") { if (v < 0 || v > 2) return bad(); h->solve_cps = v; }
   else if (k == "factor_nb") { if (v != 0 && (v < 4 || v > 64 || v % 4)) return bad(); h->factor_nb = v; }
+  else if (k == "explicit") { if (v < 0 || v > 1) return bad(); h->explicit_ops = v; }
   else if (k == "autotune") { if (v < 0 || v > 1) return bad(); h->autotune = v; }
   else { h->err = "fp_set_option: unknown key " + k; return FP_ERR_INVALID; }
   h->gdirty = 1;

@@ -1,0 +1,315 @@
+// Explicit local interface operators (Sec. 3.2 applied once per subdomain instead of once
+// per iteration): for every subdomain s, with b_s the local dofs touched by B_s,
+//   F_s = (K_s^+)_{b_s b_s}                       (so F = sum_s B_s F_s B_s^T, Eq. 3.6),
+//   S_s = K_bb - K_bi K_ii^{-1} K_ib               (the Dirichlet preconditioner, Eq. 3.5),
+// both dense m_s x m_s, built at factorisation time by multi-right-hand-side solves with
+// the band factors, and applied in the PCG loop as batched dense products.
+//
+// Build: one CTA per (subdomain, tile of MT = 32 right-hand sides), persistent over a work
+// queue.  The tile's n x MT block lives in a per-CTA global scratch; the forward and
+// backward sweeps keep the b + 32 live rows in a shared-memory window (cyclic in the row
+// index), stage the 32 factor columns of the current block and its inverse diagonal block
+// in shared memory, and do the off-block coupling as a register-tiled product (8 rows x 4
+// columns per thread in the forward sweep, 1 row x 4 columns in the backward sweep).
+// No spin-waits and no asynchronous copies: plain loads and __syncthreads only.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace fp {
+
+constexpr int MRHS_T = 32;  // right-hand sides per task
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
+  v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
+}
+
+// kind 0: F_s (right-hand sides e_{b_j}; fixed dofs of floating subdomains give zero
+// columns), kind 1: S_s (right-hand sides -K_{i, b_j} on interior rows, Dirichlet factor).
+// Task t = (subdomain task_s[t], first column task_j0[t]).
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int *task_j0, int ntask, DevTopo D,
+                                                   const T *fac, const T *linv, const long long *linv_off,
+                                                   const double *csr_val, int kind, T *scratch,
+                                                   long long scratch_stride, int *counter, T *out,
+                                                   const long long *out_off, int R, int LDp) {
+  extern __shared__ unsigned char smraw[];
+  T *Wn = reinterpret_cast<T *>(smraw);  // R x MT window
+  T *Fc = Wn + (size_t)R * MRHS_T;       // 32 x LDp staged factor columns
+  T *Lv = Fc + (size_t)32 * LDp;         // 32 x 32 inverse diagonal block
+  T *Tt = Lv + 1024;                     // 32 x MT backward temporaries
+  __shared__ int s_task;
+  const int tid = threadIdx.x, cg = tid & 7, rg = tid >> 3;
+  T *Xs = scratch + (long long)blockIdx.x * scratch_stride;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int task = s_task;
+    __syncthreads();
+    if (task >= ntask) break;
+    const int s = task_s[task], j0 = task_j0[task];
+    const DevTpl t = D.tpl[D.sub_tpl[s]];
+    const int n = t.n, LD = t.LD, b = t.b, m = t.nbnd;
+    const int ncol = min(MRHS_T, m - j0);
+    const int *bnd = D.pool + t.bnd;
+    const int *cptr = D.pool + t.csr_ptr, *ccol = D.pool + t.csr_col;
+    const int *isb = D.pool + t.is_bnd;
+    const double *val = csr_val + D.csr_off[s];
+    const T *F = fac + D.fac_off[s];
+    const T *Li = linv + linv_off[s];
+    auto fixed = [&](int d) { return t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2); };
+    // ---- right-hand sides into the scratch block (row r at Xs + r * MT) ----
+    for (long long i = tid; i < (long long)n * MRHS_T; i += blockDim.x) Xs[i] = T(0);
+    __syncthreads();
+    for (int jj = tid; jj < ncol; jj += blockDim.x) {
+      const int c = bnd[j0 + jj];
+      if (kind == 0) {
+        if (!fixed(c)) Xs[(long long)c * MRHS_T + jj] = T(1);
+      } else {
+        for (int e = cptr[c]; e < cptr[c + 1]; ++e) {
+          const int i = ccol[e];
+          if (!isb[i]) Xs[(long long)i * MRHS_T + jj] = T(-val[e]);
+        }
+      }
+    }
+    __syncthreads();
+    const int nb = (n + 31) / 32;
+    // ---- forward sweep: L y = rhs, z = D^{-1} y into Xs ----
+    int hi = 0;
+    for (int k = 0; k < nb; ++k) {
+      const int r0 = 32 * k, ncb = min(32, n - r0), rend = min(n, r0 + 32 + b);
+      for (int idx = tid; idx < (rend - hi) * MRHS_T; idx += blockDim.x) {
+        const int r = hi + idx / MRHS_T, q = idx % MRHS_T;
+        Wn[(r % R) * MRHS_T + q] = Xs[(long long)r * MRHS_T + q];
+      }
+      hi = max(hi, rend);
+      for (int idx = tid; idx < ncb * LD; idx += blockDim.x) {
+        const int c = idx / LD, sl = idx - c * LD;
+        Fc[c * LDp + sl] = F[(long long)(r0 + c) * LD + sl];
+      }
+      for (int idx = tid; idx < 1024; idx += blockDim.x) Lv[idx] = Li[(long long)k * 1024 + idx];
+      __syncthreads();
+      // diagonal block: y_k = Linv_k w_k (rows past n are never loaded: c < ncb)
+      T y[4] = {T(0), T(0), T(0), T(0)};
+      for (int c = 0; c < ncb; ++c) {
+        const T l = Lv[rg * 32 + c];
+        T w[4];
+        ld4(Wn + ((r0 + c) % R) * MRHS_T + 4 * cg, w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y[q] += l * w[q];
+      }
+      __syncthreads();
+      if (rg < ncb) {
+        const T dinv = Fc[rg * LDp + (r0 + rg) % LD];
+        T *wr = Wn + ((r0 + rg) % R) * MRHS_T + 4 * cg;
+        T *xr = Xs + (long long)(r0 + rg) * MRHS_T + 4 * cg;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          wr[q] = y[q];
+          xr[q] = y[q] * dinv;
+        }
+      }
+      __syncthreads();
+      // off-block coupling: w_r -= sum_c L(r, r0 + c) y_{r0 + c}, r in [r0 + 32, rend)
+      T acc[NR][4];
+#pragma unroll
+      for (int i = 0; i < NR; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = T(0);
+      for (int c = 0; c < ncb; ++c) {
+        T yc[4];
+        ld4(Wn + ((r0 + c) % R) * MRHS_T + 4 * cg, yc);
+        const T *col = Fc + c * LDp;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+          const int r = r0 + 32 + rg + 32 * i;
+          const T l = (r < rend && r - (r0 + c) <= b) ? col[r % LD] : T(0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[i][q] += l * yc[q];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const int r = r0 + 32 + rg + 32 * i;
+        if (r < rend) {
+          T *wr = Wn + (r % R) * MRHS_T + 4 * cg;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) wr[q] -= acc[i][q];
+        }
+      }
+      __syncthreads();
+    }
+    // ---- backward sweep: L^T x = z; x rows kept in the window and written to Xs ----
+    for (int k = nb - 1; k >= 0; --k) {
+      const int r0 = 32 * k, ncb = min(32, n - r0), rtop = min(n, r0 + 32 + b);
+      for (int idx = tid; idx < ncb * LD; idx += blockDim.x) {
+        const int c = idx / LD, sl = idx - c * LD;
+        Fc[c * LDp + sl] = F[(long long)(r0 + c) * LD + sl];
+      }
+      for (int idx = tid; idx < 1024; idx += blockDim.x) Lv[idx] = Li[(long long)k * 1024 + idx];
+      __syncthreads();
+      T tv[4] = {T(0), T(0), T(0), T(0)};
+      if (rg < ncb) {
+        ld4(Xs + (long long)(r0 + rg) * MRHS_T + 4 * cg, tv);
+        const T *col = Fc + rg * LDp;
+        const int j = r0 + rg;
+        for (int r = r0 + 32; r < rtop; ++r) {
+          const T l = (r - j <= b) ? col[r % LD] : T(0);
+          T x4[4];
+          ld4(Wn + (r % R) * MRHS_T + 4 * cg, x4);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) tv[q] -= l * x4[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Tt[rg * MRHS_T + 4 * cg + q] = tv[q];
+      __syncthreads();
+      // within the block: x_k = Linv_k^T t
+      T x[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) {
+        const T l = Lv[c * 32 + rg];
+        T tc[4];
+        ld4(Tt + c * MRHS_T + 4 * cg, tc);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] += l * tc[q];
+      }
+      if (rg < ncb) {
+        T *wr = Wn + ((r0 + rg) % R) * MRHS_T + 4 * cg;
+        T *xr = Xs + (long long)(r0 + rg) * MRHS_T + 4 * cg;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          wr[q] = x[q];
+          xr[q] = x[q];
+        }
+      }
+      __syncthreads();
+    }
+    // ---- the operator's columns j0 .. j0 + ncol - 1 ----
+    T *O = out + out_off[s];
+    const int mp = (m + 3) & ~3;  // row stride (padded to 4 for vector loads)
+    if (kind == 0) {
+      for (int idx = tid; idx < m * ncol; idx += blockDim.x) {
+        const int a = idx / ncol, jj = idx - a * ncol;
+        O[(long long)a * mp + j0 + jj] = Xs[(long long)bnd[a] * MRHS_T + jj];
+      }
+    } else {
+      // S[a][j] = sum_c K[b_a][c] (y_j[c] + [c == b_j]);  y_j vanishes on the rows of b
+      for (int idx = tid; idx < m * ncol; idx += blockDim.x) {
+        const int a = idx / ncol, jj = idx - a * ncol;
+        const int row = bnd[a], cj = bnd[j0 + jj];
+        double acc = 0.0;
+        for (int e = cptr[row]; e < cptr[row + 1]; ++e) {
+          const int c = ccol[e];
+          acc += val[e] * ((double)Xs[(long long)c * MRHS_T + jj] + (c == cj ? 1.0 : 0.0));
+        }
+        O[(long long)a * mp + j0 + jj] = T(acc);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y_b = A_s x_b for every subdomain (A_s = F_s or S_s, dense, row stride mp = m rounded up
+// to 4, pad columns zero), read from and written back to the local vectors at the rows b_s
+// (in place: x_b is staged in shared memory first).  One CTA per subdomain, one warp per
+// row, vectorised row loads; sums in the operator's precision.
+template <typename T>
+__global__ void __launch_bounds__(256) k_explicit_apply(DevTopo D, const T *ops, const long long *op_off,
+                                                        double *xloc, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  extern __shared__ unsigned char smraw[];
+  T *xs = reinterpret_cast<T *>(smraw);
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int m = t.nbnd, mp = (m + 3) & ~3;
+  const int *bnd = D.pool + t.bnd;
+  double *x = xloc + D.vec_off[s];
+  for (int q = threadIdx.x; q < mp; q += blockDim.x) xs[q] = q < m ? T(x[bnd[q]]) : T(0);
+  __syncthreads();
+  const T *A = ops + op_off[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int a = warp; a < m; a += nw) {
+    const T *row = A + (long long)a * mp;
+    T acc = T(0);
+    for (int j = 4 * lane; j < mp; j += 128) {
+      T v[4];
+      if (sizeof(T) == 4) {
+        const float4 f = *reinterpret_cast<const float4 *>(row + j);
+        v[0] = T(f.x); v[1] = T(f.y); v[2] = T(f.z); v[3] = T(f.w);
+      } else {
+        const double2 d0 = *reinterpret_cast<const double2 *>(row + j);
+        const double2 d1 = *reinterpret_cast<const double2 *>(row + j + 2);
+        v[0] = T(d0.x); v[1] = T(d0.y); v[2] = T(d1.x); v[3] = T(d1.y);
+      }
+      acc += v[0] * xs[j] + v[1] * xs[j + 1] + v[2] * xs[j + 2] + v[3] * xs[j + 3];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) x[bnd[a]] = double(acc);
+  }
+}
+
+// ------------------------------------ launchers --------------------------------------
+template <typename T, int NR>
+static cudaError_t launch_mrhs_T(int grid, cudaStream_t st, const int *ts, const int *tj, int ntask, DevTopo D,
+                                 const T *fac, const T *linv, const long long *loff, const double *csr, int kind,
+                                 T *scratch, long long sstride, int *counter, T *out, const long long *ooff, int R,
+                                 int LDp, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_band_mrhs<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_band_mrhs<T, NR><<<grid, 256, smem, st>>>(ts, tj, ntask, D, fac, linv, loff, csr, kind, scratch, sstride,
+                                              counter, out, ooff, R, LDp);
+  return cudaGetLastError();
+}
+
+size_t mrhs_smem_bytes(bool fp32, int R, int LDp) {
+  const size_t esz = fp32 ? 4 : 8;
+  return esz * ((size_t)R * MRHS_T + 32 * (size_t)LDp + 1024 + 32 * MRHS_T);
+}
+
+cudaError_t launch_band_mrhs(bool fp32, int nr, int grid, cudaStream_t st, const int *task_s, const int *task_j0,
+                             int ntask, DevTopo D, const void *fac, const void *linv, const long long *linv_off,
+                             const double *csr, int kind, void *scratch, long long sstride, int *counter, void *out,
+                             const long long *out_off, int R, int LDp) {
+  const size_t smem = mrhs_smem_bytes(fp32, R, LDp);
+#define FP_MRHS(TT, N)                                                                                        \
+  return launch_mrhs_T<TT, N>(grid, st, task_s, task_j0, ntask, D, (const TT *)fac, (const TT *)linv, linv_off, \
+                              csr, kind, (TT *)scratch, sstride, counter, (TT *)out, out_off, R, LDp, smem)
+  if (fp32) {
+    if (nr <= 4) FP_MRHS(float, 4);
+    if (nr <= 8) FP_MRHS(float, 8);
+    if (nr <= 12) FP_MRHS(float, 12);
+    FP_MRHS(float, 16);
+  }
+  if (nr <= 4) FP_MRHS(double, 4);
+  if (nr <= 8) FP_MRHS(double, 8);
+  if (nr <= 12) FP_MRHS(double, 12);
+  FP_MRHS(double, 16);
+#undef FP_MRHS
+}
+
+// resident CTAs per SM of the build kernel at this shared-memory size
+int mrhs_blocks_per_sm(bool fp32, int nr, int R, int LDp) {
+  const size_t smem = mrhs_smem_bytes(fp32, R, LDp);
+  int nb = 0;
+  const void *f = nullptr;
+  if (fp32) f = nr <= 4 ? (const void *)k_band_mrhs<float, 4> : nr <= 8 ? (const void *)k_band_mrhs<float, 8>
+              : nr <= 12 ? (const void *)k_band_mrhs<float, 12> : (const void *)k_band_mrhs<float, 16>;
+  else f = nr <= 4 ? (const void *)k_band_mrhs<double, 4> : nr <= 8 ? (const void *)k_band_mrhs<double, 8>
+           : nr <= 12 ? (const void *)k_band_mrhs<double, 12> : (const void *)k_band_mrhs<double, 16>;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, 256, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_explicit_apply(bool fp32, DevTopo D, int S, int mmax_bnd, const void *ops, const long long *op_off,
+                                  double *xloc, const int *fl, cudaStream_t st) {
+  const size_t smem = (size_t)((mmax_bnd + 3) & ~3) * (fp32 ? 4 : 8);
+  if (fp32) k_explicit_apply<float><<<S, 256, smem, st>>>(D, (const float *)ops, op_off, xloc, fl);
+  else k_explicit_apply<double><<<S, 256, smem, st>>>(D, (const double *)ops, op_off, xloc, fl);
+  return cudaGetLastError();
+}
+
+}  // namespace fp

@@ -69,7 +69,8 @@ class KernelStats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("factor_nb", ctypes.c_int), ("solve_wpc", ctypes.c_int), ("solve_chunk", ctypes.c_int),
                 ("solve_ctas_per_sm", ctypes.c_int), ("factor_ms", ctypes.c_double),
-                ("solve_ms", ctypes.c_double), ("candidates", ctypes.c_int)]
+                ("solve_ms", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("explicit_ms", ctypes.c_double)]
 
 
 class StepStats(ctypes.Structure):

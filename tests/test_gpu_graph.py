@@ -53,12 +53,14 @@ def _same(a, b):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("explicit", [0, 1])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_graph_matches_stream_bitwise(F, precision):
+def test_graph_matches_stream_bitwise(F, precision, explicit):
     case = W.small_case(3, 4, 5, k=2, lame_lambda=49.0, tau=1e-3, n_steps=4, tol=1e-10,
                         source="manufactured_t")
-    a = _run(F, case, 0, 4, precision=precision)
-    b = _run(F, case, 1, 4, precision=precision)
+    opts = (("explicit", explicit),)
+    a = _run(F, case, 0, 4, opts=opts, precision=precision)
+    b = _run(F, case, 1, 4, opts=opts, precision=precision)
     _same(a, b)
     assert all(s["true_rel_residual"] <= 1e-10 for s in b[0])
 

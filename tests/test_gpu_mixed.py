@@ -39,13 +39,17 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("explicit", [0, 1])
 @pytest.mark.parametrize("case", CASES)
-def test_mixed_steps_match_oracle(F, case):
+def test_mixed_steps_match_oracle(F, case, explicit):
+    """explicit = 1: the PCG loop applies F and the preconditioner through FP32 dense local
+    operators; the accurate applies keep the refined band solves."""
     from oracle.monolithic import Discretization, solve_monolithic
     d = Discretization(case)
     mono = solve_monolithic(case, d)
     sol = F.Solver(case)
     sol.set_option("ir_eps", 1e-15)
+    sol.set_option("explicit", explicit)
     sol.assemble()
     sol.factor()
     for n in range(case.n_steps):

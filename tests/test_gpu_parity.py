@@ -81,9 +81,13 @@ OPS_CASES = [
 ]
 
 
+@pytest.mark.parametrize("explicit", [0, 1])
 @pytest.mark.parametrize("case", OPS_CASES)
-def test_interface_operators(F, case):
+def test_interface_operators(F, case, explicit):
+    """explicit = 1: F and the Dirichlet preconditioner applied through the dense local
+    operators F_s, S_s built by the multi-right-hand-side band solves."""
     sol = F.Solver(case)
+    sol.set_option("explicit", explicit)
     sol.assemble()
     sol.factor()
     d, fe = _oracle(case)
@@ -108,12 +112,14 @@ STEP_CASES = [
 ]
 
 
+@pytest.mark.parametrize("explicit", [0, 1])
 @pytest.mark.parametrize("case", STEP_CASES)
-def test_steps_match_oracle(F, case):
+def test_steps_match_oracle(F, case, explicit):
     from oracle.monolithic import solve_monolithic
     d, _ = _oracle(case)
     mono = solve_monolithic(case, d)
     sol = F.Solver(case)
+    sol.set_option("explicit", explicit)
     sol.assemble()
     sol.factor()
     for n in range(case.n_steps):
