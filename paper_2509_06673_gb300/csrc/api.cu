@@ -36,6 +36,10 @@ cudaError_t launch_band_mrhs(bool fp32, int nr, int grid, cudaStream_t st, const
 int mrhs_blocks_per_sm(bool fp32, int nr, int R, int LDp);
 cudaError_t launch_explicit_apply(bool fp32, DevTopo D, int S, int mmax_bnd, const void *ops, const long long *op_off,
                                   double *xloc, const int *fl, cudaStream_t st);
+cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, const long long *full_off,
+                            float *tiles, const long long *tile_off, cudaStream_t st);
+cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
+                                      double *xloc, const int *fl, cudaStream_t st);
 __global__ void k_dot(const double *, const double *, long long, double *, unsigned *, double *, int *, int,
                       double *, int);
 __global__ void k_pcg_update(double *, double *, const double *, const double *, long long, double *, unsigned *,
@@ -48,7 +52,8 @@ __global__ void k_wscale(DevTopo, const double *, double *, const int *);
 __global__ void k_halo(DevTopo, const double *, const double *, double *, const int *);
 __global__ void k_bnd_apply(DevTopo, const double *, const double *, double *, const int *);
 __global__ void k_Gt(DevTopo, const double *, double *, const int *);
-__global__ void k_gemv(const double *, const double *, double *, int, const int *);
+cudaError_t launch_gemv(bool fp32, const void *H, const double *y, double *alpha, int nH, const int *fl,
+                        cudaStream_t st);
 __global__ void k_Gcomb(DevTopo, const double *, const double *, double, double *, const int *);
 __global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, const double *,
                       const double *, double *, double *);
@@ -125,10 +130,11 @@ struct fp_handle {
   fp_tuning tuning{};
   // explicit local interface operators F_s, S_s (dense, per subdomain; option "explicit")
   int explicit_ops = 0, ops_ready = 0, opF64_ready = 0;
-  void *opF = nullptr, *opS = nullptr;  // the PCG loop's operators (factor precision)
+  // the PCG loop's operators: FP64 full m x mp matrices (FP64), FP32 upper 32 x 32 tiles (mixed)
+  void *opF = nullptr, *opS = nullptr;
   double *opF64 = nullptr;              // mixed precision: F_s in FP64 for the accurate applies
-  const long long *op_off = nullptr, *linv_off_dev = nullptr;
-  long long op_total = 0;
+  const long long *op_off = nullptr, *tile_off = nullptr, *linv_off_dev = nullptr;
+  long long op_total = 0, tile_total = 0;
   const int *mrhs_s = nullptr, *mrhs_j0 = nullptr;
   int mrhs_ntask = 0;
   double explicit_build_ms = 0;
@@ -334,19 +340,22 @@ fp_status build_device(fp_handle *h) {
   {
     // explicit-operator layout (rows padded to a multiple of 4) and build tasks: every
     // subdomain in cost order, tiles of 32 right-hand sides
-    std::vector<long long> ooff(T.S + 1, 0);
+    std::vector<long long> ooff(T.S + 1, 0), toff(T.S + 1, 0);
     std::vector<int> ms, mj;
     for (int s = 0; s < T.S; ++s) {
-      const long long m = (long long)T.tpl[T.sub_tpl[s]].bnd.size();
+      const long long m = (long long)T.tpl[T.sub_tpl[s]].bnd.size(), nt = (m + 31) / 32;
       ooff[s + 1] = ooff[s] + m * ((m + 3) & ~3LL);
+      toff[s + 1] = toff[s] + nt * (nt + 1) / 2 * 1024;
     }
     for (int s : order) {
       const int m = (int)T.tpl[T.sub_tpl[s]].bnd.size();
       for (int j0 = 0; j0 < m; j0 += 32) { ms.push_back(s); mj.push_back(j0); }
     }
     h->op_total = ooff[T.S];
+    h->tile_total = toff[T.S];
     h->mrhs_ntask = (int)ms.size();
     TRY(upload(h, &h->op_off, ooff));
+    TRY(upload(h, &h->tile_off, toff));
     TRY(upload(h, &h->mrhs_s, ms));
     TRY(upload(h, &h->mrhs_j0, mj));
   }
@@ -357,6 +366,7 @@ fp_status build_device(fp_handle *h) {
     tk.push_back({T.fac_off[s], T.vec_off[s], linv_off[s], t.n, t.LD, t.b, 0});
     mmax = std::max(mmax, t.LD / 32);
   }
+  if (T.nH > 28672) { h->err = "coarse space above 28672 unknowns is not supported"; return FP_ERR_INVALID; }
   if (mmax > 16) { h->err = "half bandwidth above 511 is not supported"; return FP_ERR_INVALID; }
   h->mmax = mmax <= 4 ? 4 : mmax <= 8 ? 8 : mmax <= 12 ? 12 : 16;
   h->ntask = T.S;
@@ -591,6 +601,8 @@ fp_status solve_refined(fp_handle *h, const double *b, double *x, int sweeps, co
   return FP_OK;
 }
 
+// out = P v (FP64 throughout: an FP32 copy of (G^T G)^{-1} in the PCG loop let lambda drift
+// off G^T lambda = e far enough to force restarts on config 5)
 fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
   const int nl = h->T.n_lambda;
   if (!h->T.NF) {
@@ -598,7 +610,8 @@ fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
     return FP_OK;
   }
   k_Gt<<<(h->T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->cy, fl);
-  k_gemv<<<(h->T.nH * 32 + 255) / 256, 256, 0, h->stream>>>(h->Hinv, h->cy, h->calpha, h->T.nH, fl);
+  CKL();
+  CK(launch_gemv(false, h->Hinv, h->cy, h->calpha, h->T.nH, fl, h->stream));
   k_Gcomb<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->calpha, v, -1.0, out, fl);
   CKL();
   return FP_OK;
@@ -617,7 +630,10 @@ fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, boo
   const void *op = nullptr;
   if (h->ops_ready) op = !mixed || !accurate ? h->opF : (h->opF64_ready ? h->opF64 : nullptr);
   if (op) {
-    CK(launch_explicit_apply(mixed && !accurate, h->D, h->T.S, h->nbnd_max, op, h->op_off, h->XB, fl, h->stream));
+    if (mixed && !accurate)
+      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)op, h->tile_off, h->XB, fl, h->stream));
+    else
+      CK(launch_explicit_apply(false, h->D, h->T.S, h->nbnd_max, op, h->op_off, h->XB, fl, h->stream));
     k_gather<<<(h->T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->XB, out, fl);
     CKL();
     return FP_OK;
@@ -646,8 +662,11 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
   k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl);
   CKL();
   if (h->ops_ready) {
-    CK(launch_explicit_apply(h->P.precision == FP_PREC_MIXED, h->D, h->T.S, h->nbnd_max, h->opS, h->op_off, h->XP,
-                             fl, h->stream));
+    if (h->P.precision == FP_PREC_MIXED)
+      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)h->opS, h->tile_off, h->XP, fl,
+                                   h->stream));
+    else
+      CK(launch_explicit_apply(false, h->D, h->T.S, h->nbnd_max, h->opS, h->op_off, h->XP, fl, h->stream));
   } else {
     k_halo<<<h->T.S, 256, 0, h->stream>>>(h->D, h->csr_val, h->XP, h->XY, fl);
     CKL();
@@ -749,7 +768,7 @@ fp_status build_features(fp_handle *h) {
 
 fp_status choose_nb(fp_handle *h, bool dbl, const BandTask *tasks, void *buf, int *nb_out);
 fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, int kind, void *out);
-fp_status alloc_op(fp_handle *h, void **p, size_t esz);
+fp_status alloc_op(fp_handle *h, void **p, size_t bytes);
 
 template <typename T>
 fp_status factor_T(fp_handle *h) {
@@ -790,11 +809,11 @@ fp_status factor_T(fp_handle *h) {
       if (st == FP_OK && mode == 0 && h->explicit_ops) {
         // F_s in FP64 from the FP64 factor (the accurate applies), and its FP32 rounding (the
         // PCG loop's operator)
-        st = alloc_op(h, (void **)&h->opF64, 8);
-        if (st == FP_OK) st = alloc_op(h, &h->opF, 4);
+        st = alloc_op(h, (void **)&h->opF64, (size_t)h->op_total * 8);
+        if (st == FP_OK) st = alloc_op(h, &h->opF, (size_t)h->tile_total * 4);
         if (st == FP_OK) st = run_mrhs(h, false, tN, tL, 0, h->opF64);
         if (st == FP_OK) {
-          ee = launch_round_to_float(h->opF64, (float *)h->opF, h->op_total, h->stream);
+          ee = launch_pack_sym(true, h->D, h->T.S, h->opF64, h->op_off, (float *)h->opF, h->tile_off, h->stream);
           if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
         }
         if (st == FP_OK) h->opF64_ready = 1;
@@ -962,23 +981,43 @@ fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, i
   return FP_OK;
 }
 
-fp_status alloc_op(fp_handle *h, void **p, size_t esz) {
+fp_status alloc_op(fp_handle *h, void **p, size_t bytes) {
   if (!*p) {
-    CK(cudaMalloc(p, (size_t)h->op_total * esz));
+    CK(cudaMalloc(p, bytes));
     h->allocs.push_back(*p);
   }
   return FP_OK;
 }
 
-// FP64: F_s and S_s in FP64.  Mixed: S_s in FP32 from the FP32 Dirichlet factors; F_s in FP32
-// unless the factorisation already formed it in FP64 (then opF is that, rounded once).
+// FP64: F_s and S_s in FP64, full.  Mixed: the loop's F_s and S_s as FP32 symmetric tiles;
+// F_s is the FP64 one of the factorisation rounded when it exists, else formed in FP32;
+// S_s is formed in FP32 from the FP32 Dirichlet factors.
 fp_status build_explicit(fp_handle *h) {
-  const bool fp32 = h->P.precision == FP_PREC_MIXED;
-  const size_t esz = fp32 ? 4 : 8;
-  TRY(alloc_op(h, &h->opF, esz));
-  TRY(alloc_op(h, &h->opS, esz));
-  if (!h->opF64_ready) TRY(run_mrhs(h, fp32, h->facN, h->linvN, 0, h->opF));
-  TRY(run_mrhs(h, fp32, h->facD, h->linvD, 1, h->opS));
+  if (h->P.precision == FP_PREC_FP64) {
+    TRY(alloc_op(h, &h->opF, (size_t)h->op_total * 8));
+    TRY(alloc_op(h, &h->opS, (size_t)h->op_total * 8));
+    TRY(run_mrhs(h, false, h->facN, h->linvN, 0, h->opF));
+    TRY(run_mrhs(h, false, h->facD, h->linvD, 1, h->opS));
+    h->ops_ready = 1;
+    return FP_OK;
+  }
+  TRY(alloc_op(h, &h->opF, (size_t)h->tile_total * 4));
+  TRY(alloc_op(h, &h->opS, (size_t)h->tile_total * 4));
+  void *full = nullptr;
+  CK(cudaMalloc(&full, (size_t)h->op_total * 4));
+  fp_status st = FP_OK;
+  if (!h->opF64_ready) {
+    st = run_mrhs(h, true, h->facN, h->linvN, 0, full);
+    if (st == FP_OK && launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opF, h->tile_off,
+                                       h->stream) != cudaSuccess) { h->err = "pack"; st = FP_ERR_CUDA; }
+  }
+  if (st == FP_OK) st = run_mrhs(h, true, h->facD, h->linvD, 1, full);
+  if (st == FP_OK && launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opS, h->tile_off,
+                                     h->stream) != cudaSuccess) { h->err = "pack"; st = FP_ERR_CUDA; }
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFree(full);
+  if (st != FP_OK) return st;
+  if (e != cudaSuccess) { h->err = cudaGetErrorString(e); return FP_ERR_CUDA; }
   h->ops_ready = 1;
   return FP_OK;
 }
@@ -1024,7 +1063,7 @@ fp_status step_prologue(fp_handle *h, bool use_learned) {
   CKL();
   // lambda_00 = G (G^T G)^{-1} e ; lambda_0 = lambda_00 + P lambda^{n-1}
   if (T.NF) {
-    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->ce, h->calpha, T.nH, nullptr);
+    CK(launch_gemv(false, h->Hinv, h->ce, h->calpha, T.nH, nullptr, s));
     k_Gcomb<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->calpha, nullptr, 1.0, h->lam00, nullptr);
     CKL();
   } else {
@@ -1229,7 +1268,7 @@ fp_status step_recovery(fp_handle *h) {
   if (T.NF) {
     TRY(lincomb(h, h->t1, h->t2, 1.0, h->d, -1.0, nullptr));
     k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr);
-    k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, s>>>(h->Hinv, h->cy, h->calpha, T.nH, nullptr);
+    CK(launch_gemv(false, h->Hinv, h->cy, h->calpha, T.nH, nullptr, s));
     CKL();
   }
   if (h->ops_ready && (h->P.precision == FP_PREC_FP64 || h->opF64_ready)) {
@@ -1857,9 +1896,10 @@ extern "C" fp_status fp_apply_projection_noalloc(fp_handle *h, const double *v, 
       }
       double *cy = scratch, *ca = scratch + kNoAllocMaxCoarse;
       k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, cy, h->fl_zero);
-      k_gemv<<<(T.nH * 32 + 255) / 256, 256, 0, h->stream>>>(h->Hinv, cy, ca, T.nH, h->fl_zero);
+      cudaError_t e = launch_gemv(false, h->Hinv, cy, ca, T.nH, h->fl_zero, h->stream);
+      if (e != cudaSuccess) { h->err = std::string("kernel launch: ") + cudaGetErrorString(e); st = FP_ERR_CUDA; break; }
       k_Gcomb<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, ca, v, -1.0, out, h->fl_zero);
-      cudaError_t e = cudaGetLastError();
+      e = cudaGetLastError();
       if (e != cudaSuccess) { h->err = std::string("kernel launch: ") + cudaGetErrorString(e); st = FP_ERR_CUDA; break; }
     }
     cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -251,6 +251,116 @@ __global__ void __launch_bounds__(256) k_explicit_apply(DevTopo D, const T *ops,
   }
 }
 
+// ---------------------------- symmetric tiled FP32 operators ----------------------------
+// The PCG loop's FP32 operators are stored as the upper 32 x 32 tiles (I <= J) of A_s, tile
+// index I nt - I (I - 1) / 2 + (J - I) with nt = ceil(m / 32), row-major inside a tile and
+// zero past m: about half the bytes of the full matrix, and exactly symmetric.
+__device__ __forceinline__ void tile_ij(int tile, int nt, int &I, int &J) {
+  I = 0;
+  while (tile >= nt - I) {
+    tile -= nt - I;
+    ++I;
+  }
+  J = I + tile;
+}
+
+template <typename Tin>
+__global__ void k_pack_sym(DevTopo D, const Tin *full, const long long *full_off, float *tiles,
+                           const long long *tile_off) {
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int m = t.nbnd, mp = (m + 3) & ~3, nt = (m + 31) / 32, ntile = nt * (nt + 1) / 2;
+  const Tin *Fm = full + full_off[s];
+  float *Tm = tiles + tile_off[s];
+  for (long long idx = threadIdx.x; idx < (long long)ntile * 1024; idx += blockDim.x) {
+    int I, J;
+    tile_ij((int)(idx >> 10), nt, I, J);
+    const int e = (int)(idx & 1023), a = 32 * I + (e >> 5), j = 32 * J + (e & 31);
+    Tm[idx] = (a < m && j < m) ? float(Fm[(long long)a * mp + j]) : 0.0f;
+  }
+}
+
+// y_b = A_s x_b for the tiled symmetric A_s, in place on the local vectors at the rows b_s.
+// Warp w takes tiles w, w + 8, ...; lane c holds column c of a tile (one coalesced 128-byte
+// row per load).  An off-diagonal tile gives A_IJ^T x_I to y_J (a per-lane sum) and A_IJ x_J
+// to y_I: the 32 row sums come out of a transposing butterfly (at offset k a lane keeps the
+// half of its values selected by bit k of its lane index and adds the partner's copy of that
+// half: 31 shuffles, and lane l ends with row sum l).  Partial sums land in shared memory and
+// are added in a fixed order.
+__global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const float *tiles, const long long *tile_off,
+                                                            double *xloc, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  extern __shared__ float smf[];
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int m = t.nbnd, nt = (m + 31) / 32, ntile = nt * (nt + 1) / 2;
+  float *xs = smf;                 // nt * 32
+  float *rp = xs + nt * 32;        // ntile * 32 row-part sums
+  float *cp = rp + ntile * 32;     // ntile * 32 column-part sums
+  const int *bnd = D.pool + t.bnd;
+  double *x = xloc + D.vec_off[s];
+  for (int q = threadIdx.x; q < nt * 32; q += blockDim.x) xs[q] = q < m ? float(x[bnd[q]]) : 0.0f;
+  __syncthreads();
+  const float *A = tiles + tile_off[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int tile = warp; tile < ntile; tile += nw) {
+    int I, J;
+    tile_ij(tile, nt, I, J);
+    const float *T = A + (long long)tile * 1024;
+    float v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = T[r * 32 + lane];
+    if (I < J) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc += v[r] * xs[32 * I + r];
+      cp[tile * 32 + lane] = acc;
+    }
+    const float xj = xs[32 * J + lane];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] *= xj;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+      const bool up = (lane & k) != 0;
+#pragma unroll
+      for (int i = 0; i < k; ++i) {
+        const float send = up ? v[i] : v[i + k];
+        const float keep = up ? v[i + k] : v[i];
+        v[i] = keep + __shfl_xor_sync(FULL, send, k);
+      }
+    }
+    rp[tile * 32 + lane] = v[0];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int I = i >> 5, r = i & 31;
+    const int row0 = I * nt - I * (I - 1) / 2;  // tile index of (I, I)
+    float y = 0.0f;
+    for (int J = I; J < nt; ++J) y += rp[(row0 + J - I) * 32 + r];
+    for (int I2 = 0; I2 < I; ++I2) y += cp[(I2 * nt - I2 * (I2 - 1) / 2 + I - I2) * 32 + r];
+    x[bnd[i]] = double(y);
+  }
+}
+
+cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, const long long *full_off,
+                            float *tiles, const long long *tile_off, cudaStream_t st) {
+  if (src_fp64) k_pack_sym<double><<<S, 256, 0, st>>>(D, (const double *)full, full_off, tiles, tile_off);
+  else k_pack_sym<float><<<S, 256, 0, st>>>(D, (const float *)full, full_off, tiles, tile_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
+                                      double *xloc, const int *fl, cudaStream_t st) {
+  const int nt = (mmax_bnd + 31) / 32;
+  const size_t smem = sizeof(float) * ((size_t)nt * 32 + (size_t)nt * (nt + 1) * 32);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_explicit_apply_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_explicit_apply_sym<<<S, 256, smem, st>>>(D, tiles, tile_off, xloc, fl);
+  return cudaGetLastError();
+}
+
 // ------------------------------------ launchers --------------------------------------
 template <typename T, int NR>
 static cudaError_t launch_mrhs_T(int grid, cudaStream_t st, const int *ts, const int *tj, int ntask, DevTopo D,

@@ -280,10 +280,13 @@ __global__ void k_residual_N(DevTopo D, const double *__restrict__ sell_val, con
   }
 }
 
-// Refinement stop test: after x += r, skip further sweeps once ||r|| <= eps ||x|| (2-norms
-// over all subdomains), or, with stag2 > 0, once the correction stagnates: ||r||^2 >
-// stag2 ||r_prev||^2 means the sweeps have reached the rounding floor of the FP64 residual.
-// prev2 holds ||r_prev||^2 (0 before the first sweep).  Counts sweeps in fl[FL_IRSWEEPS].
+// Refinement stop test: after x += r (r the correction of this sweep), skip further sweeps
+// once ||r|| <= eps ||x|| (2-norms over all subdomains); or once the predicted next
+// correction, ||r|| times the contraction ||r|| / ||r_prev|| of the last sweep, is below
+// eps ||x|| (a converging sweep multiplies the error by the FP32 solve's relative accuracy,
+// so x is then already that accurate); or, with stag2 > 0, once the correction stagnates
+// (||r||^2 > stag2 ||r_prev||^2: the rounding floor of the FP64 residual).  prev2 holds
+// ||r_prev||^2 (0 before the first sweep).  Counts sweeps in fl[FL_IRSWEEPS].
 __global__ void k_ir_check(const double *x, const double *r, long long n, double eps2, double *partial,
                            unsigned *counter, int *fl, double *prev2, double stag2) {
   if (fl[FL_IRSKIP]) return;
@@ -301,7 +304,9 @@ __global__ void k_ir_check(const double *x, const double *r, long long n, double
     double t1 = 0.0;
     for (int i = 0; i < (int)gridDim.x; ++i) t1 += ((volatile double *)partial)[i];
     fl[FL_IRSWEEPS] += 1;
-    if (t1 <= eps2 * tx || !(t1 == t1) || (stag2 > 0.0 && *prev2 > 0.0 && t1 > stag2 * *prev2))
+    const double p2 = *prev2;
+    if (t1 <= eps2 * tx || !(t1 == t1) || (p2 > 0.0 && t1 * t1 <= eps2 * tx * p2) ||
+        (stag2 > 0.0 && p2 > 0.0 && t1 > stag2 * p2))
       fl[FL_IRSKIP] = 1;
     *prev2 = t1;
   }
@@ -332,17 +337,51 @@ __global__ void k_Gt(DevTopo D, const double *v, double *y, const int *fl) {
   if (lane == 0) { y[3 * f] = a0; y[3 * f + 1] = a1; y[3 * f + 2] = a2; }
 }
 
-// alpha = Hinv y : dense symmetric (G^T G)^{-1}, one warp per row
-__global__ void k_gemv(const double *Hinv, const double *y, double *alpha, int nH, const int *fl) {
+// alpha = H y with H = (G^T G)^{-1} dense nH x nH (row-major), in T (FP64, or an FP32 copy
+// for the mixed-precision PCG loop).  A CTA handles GEMV_ROWS rows with y staged once in
+// shared memory (as T); a warp per row, four independent partial sums per lane; fixed order.
+constexpr int GEMV_ROWS = 32;
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv(const T *H, const double *y, double *alpha, int nH, const int *fl) {
   if (fl && fl[FL_DONE]) return;
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= nH) return;
-  const double *h = Hinv + (long long)row * nH;
-  double acc = 0.0;
-  for (int c = lane; c < nH; c += 32) acc += h[c] * y[c];
-  acc = warp_sum(acc);
-  if (lane == 0) alpha[row] = acc;
+  extern __shared__ unsigned char smraw[];
+  T *ys = reinterpret_cast<T *>(smraw);
+  for (int c = threadIdx.x; c < nH; c += blockDim.x) ys[c] = T(y[c]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r0 = blockIdx.x * GEMV_ROWS;
+  for (int row = r0 + warp; row < min(nH, r0 + GEMV_ROWS); row += blockDim.x >> 5) {
+    const T *h = H + (long long)row * nH;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int c = lane;
+    for (; c + 96 < nH; c += 128) {
+      a0 += h[c] * ys[c];
+      a1 += h[c + 32] * ys[c + 32];
+      a2 += h[c + 64] * ys[c + 64];
+      a3 += h[c + 96] * ys[c + 96];
+    }
+    for (; c < nH; c += 32) a0 += h[c] * ys[c];
+    const T acc = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) alpha[row] = double(acc);
+  }
+}
+template __global__ void k_gemv<double>(const double *, const double *, double *, int, const int *);
+template __global__ void k_gemv<float>(const float *, const double *, double *, int, const int *);
+
+cudaError_t launch_gemv(bool fp32, const void *H, const double *y, double *alpha, int nH, const int *fl,
+                        cudaStream_t st) {
+  const unsigned grid = (unsigned)((nH + GEMV_ROWS - 1) / GEMV_ROWS);
+  const size_t smem = (size_t)nH * (fp32 ? 4 : 8);
+  if (fp32) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gemv<float><<<grid, 256, smem, st>>>((const float *)H, y, alpha, nH, fl);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gemv<double><<<grid, 256, smem, st>>>((const double *)H, y, alpha, nH, fl);
+  }
+  return cudaGetLastError();
 }
 
 // out = v + sgn * G alpha  (v may be null)
