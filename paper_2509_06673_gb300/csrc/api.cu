@@ -52,8 +52,7 @@ __global__ void k_wscale(DevTopo, const double *, double *, const int *);
 __global__ void k_halo(DevTopo, const double *, const double *, double *, const int *);
 __global__ void k_bnd_apply(DevTopo, const double *, const double *, double *, const int *);
 __global__ void k_Gt(DevTopo, const double *, double *, const int *);
-cudaError_t launch_gemv(bool fp32, const void *H, const double *y, double *alpha, int nH, const int *fl,
-                        cudaStream_t st);
+cudaError_t launch_gemv(const double *H, const double *y, double *alpha, int nH, const int *fl, cudaStream_t st);
 __global__ void k_Gcomb(DevTopo, const double *, const double *, double, double *, const int *);
 __global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, const double *,
                       const double *, double *, double *);
@@ -611,7 +610,7 @@ fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
   }
   k_Gt<<<(h->T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->cy, fl);
   CKL();
-  CK(launch_gemv(false, h->Hinv, h->cy, h->calpha, h->T.nH, fl, h->stream));
+  CK(launch_gemv(h->Hinv, h->cy, h->calpha, h->T.nH, fl, h->stream));
   k_Gcomb<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->calpha, v, -1.0, out, fl);
   CKL();
   return FP_OK;
@@ -1063,7 +1062,7 @@ fp_status step_prologue(fp_handle *h, bool use_learned) {
   CKL();
   // lambda_00 = G (G^T G)^{-1} e ; lambda_0 = lambda_00 + P lambda^{n-1}
   if (T.NF) {
-    CK(launch_gemv(false, h->Hinv, h->ce, h->calpha, T.nH, nullptr, s));
+    CK(launch_gemv(h->Hinv, h->ce, h->calpha, T.nH, nullptr, s));
     k_Gcomb<<<(nl + 255) / 256, 256, 0, s>>>(h->D, h->calpha, nullptr, 1.0, h->lam00, nullptr);
     CKL();
   } else {
@@ -1268,7 +1267,7 @@ fp_status step_recovery(fp_handle *h) {
   if (T.NF) {
     TRY(lincomb(h, h->t1, h->t2, 1.0, h->d, -1.0, nullptr));
     k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr);
-    CK(launch_gemv(false, h->Hinv, h->cy, h->calpha, T.nH, nullptr, s));
+    CK(launch_gemv(h->Hinv, h->cy, h->calpha, T.nH, nullptr, s));
     CKL();
   }
   if (h->ops_ready && (h->P.precision == FP_PREC_FP64 || h->opF64_ready)) {
@@ -1896,7 +1895,7 @@ extern "C" fp_status fp_apply_projection_noalloc(fp_handle *h, const double *v, 
       }
       double *cy = scratch, *ca = scratch + kNoAllocMaxCoarse;
       k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, cy, h->fl_zero);
-      cudaError_t e = launch_gemv(false, h->Hinv, cy, ca, T.nH, h->fl_zero, h->stream);
+      cudaError_t e = launch_gemv(h->Hinv, cy, ca, T.nH, h->fl_zero, h->stream);
       if (e != cudaSuccess) { h->err = std::string("kernel launch: ") + cudaGetErrorString(e); st = FP_ERR_CUDA; break; }
       k_Gcomb<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, ca, v, -1.0, out, h->fl_zero);
       e = cudaGetLastError();

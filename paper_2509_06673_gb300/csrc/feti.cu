@@ -337,50 +337,32 @@ __global__ void k_Gt(DevTopo D, const double *v, double *y, const int *fl) {
   if (lane == 0) { y[3 * f] = a0; y[3 * f + 1] = a1; y[3 * f + 2] = a2; }
 }
 
-// alpha = H y with H = (G^T G)^{-1} dense nH x nH (row-major), in T (FP64, or an FP32 copy
-// for the mixed-precision PCG loop).  A CTA handles GEMV_ROWS rows with y staged once in
-// shared memory (as T); a warp per row, four independent partial sums per lane; fixed order.
-constexpr int GEMV_ROWS = 32;
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemv(const T *H, const double *y, double *alpha, int nH, const int *fl) {
+// alpha = H y with H = (G^T G)^{-1} dense nH x nH (row-major, FP64): one warp per row, y
+// read through the cache (it is reused by every row), four independent partial sums per
+// lane for more loads in flight; fixed order.  (Staging y in shared memory per CTA was
+// slower: every CTA re-reads the whole of y.)
+__global__ void __launch_bounds__(256) k_gemv(const double *__restrict__ H, const double *__restrict__ y,
+                                              double *alpha, int nH, const int *fl) {
   if (fl && fl[FL_DONE]) return;
-  extern __shared__ unsigned char smraw[];
-  T *ys = reinterpret_cast<T *>(smraw);
-  for (int c = threadIdx.x; c < nH; c += blockDim.x) ys[c] = T(y[c]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r0 = blockIdx.x * GEMV_ROWS;
-  for (int row = r0 + warp; row < min(nH, r0 + GEMV_ROWS); row += blockDim.x >> 5) {
-    const T *h = H + (long long)row * nH;
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    int c = lane;
-    for (; c + 96 < nH; c += 128) {
-      a0 += h[c] * ys[c];
-      a1 += h[c + 32] * ys[c + 32];
-      a2 += h[c + 64] * ys[c + 64];
-      a3 += h[c + 96] * ys[c + 96];
-    }
-    for (; c < nH; c += 32) a0 += h[c] * ys[c];
-    const T acc = warp_sum((a0 + a1) + (a2 + a3));
-    if (lane == 0) alpha[row] = double(acc);
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nH) return;
+  const double *h = H + (long long)row * nH;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = lane;
+  for (; c + 96 < nH; c += 128) {
+    a0 += h[c] * __ldg(y + c);
+    a1 += h[c + 32] * __ldg(y + c + 32);
+    a2 += h[c + 64] * __ldg(y + c + 64);
+    a3 += h[c + 96] * __ldg(y + c + 96);
   }
+  for (; c < nH; c += 32) a0 += h[c] * __ldg(y + c);
+  const double acc = warp_sum((a0 + a1) + (a2 + a3));
+  if (lane == 0) alpha[row] = acc;
 }
-template __global__ void k_gemv<double>(const double *, const double *, double *, int, const int *);
-template __global__ void k_gemv<float>(const float *, const double *, double *, int, const int *);
 
-cudaError_t launch_gemv(bool fp32, const void *H, const double *y, double *alpha, int nH, const int *fl,
-                        cudaStream_t st) {
-  const unsigned grid = (unsigned)((nH + GEMV_ROWS - 1) / GEMV_ROWS);
-  const size_t smem = (size_t)nH * (fp32 ? 4 : 8);
-  if (fp32) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gemv<float><<<grid, 256, smem, st>>>((const float *)H, y, alpha, nH, fl);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gemv<double><<<grid, 256, smem, st>>>((const double *)H, y, alpha, nH, fl);
-  }
+cudaError_t launch_gemv(const double *H, const double *y, double *alpha, int nH, const int *fl, cudaStream_t st) {
+  k_gemv<<<(unsigned)(((long long)nH * 32 + 255) / 256), 256, 0, st>>>(H, y, alpha, nH, fl);
   return cudaGetLastError();
 }
 
