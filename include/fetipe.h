@@ -151,6 +151,17 @@ fp_status fp_factor(fp_handle *h);
  * the last iterate kept. */
 fp_status fp_step(fp_handle *h, fp_step_stats *stats);
 
+/* Initial conditions (Sec. 2.5): replaces the initial state that fp_assemble set (R eta^0
+ * from the configured source's closed-form initial data, zero for the point source) by the
+ * one of the given nodal fields: eta_0 = c0 p0 + alpha div u0 (Eq. 2.17), R eta^0 =
+ * (eta_0, phi_i) over every poroelastic subdomain with u0, p0 interpolated in P_k and P1
+ * (every node, Dirichlet nodes included).  u0, p0: host arrays in the layout of
+ * fp_get_fields (u 2 per displacement node, p one per P1 node, subdomains in id order),
+ * NULL for zero.  Also resets the step counter and the lambda history to zero; the given
+ * fields are what fp_get_fields returns until the first step.  After fp_assemble
+ * (FP_ERR_STATE before). */
+fp_status fp_set_initial(fp_handle *h, const double *u0, const double *p0);
+
 /* Runs n_steps steps back to back (same as calling fp_step n_steps times). */
 fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last);
 
@@ -171,6 +182,23 @@ fp_status fp_get_lambda_keys(const fp_handle *h, int *keys);
  * are zero on elastic subdomains.  Any pointer may be NULL. */
 fp_status fp_get_fields(const fp_handle *h, double *u, double *xi, double *eta, double *p,
                         int on_device);
+
+/* The same fields of one subdomain s (0 <= s < nsub_x * nsub_y, id = row * nsub_x + column):
+ * u 2 (k*nx+1)(k*ny+1) doubles, xi, eta, p (nx+1)(ny+1) doubles each.  Any pointer may be
+ * NULL.  FP_ERR_INVALID for s out of range. */
+fp_status fp_get_subdomain(const fp_handle *h, int s, double *u, double *xi, double *eta, double *p,
+                           int on_device);
+
+/* Checkpoint / restore of the time-stepping state: step counter, lambda^n, lambda^{n-1},
+ * R eta^n, the last fields, the source-signal history and the learned-guess network (its
+ * parameters, Adam moments and step, and whether it is in use).  Not stored: matrices and
+ * factors (fp_assemble / fp_factor rebuild them bit for bit), options, recorded training
+ * samples.  fp_restore needs a handle of the same problem after fp_assemble (FP_ERR_STATE
+ * before; FP_ERR_INVALID for a file of another problem, a bad or truncated file); the
+ * next fp_step continues exactly where the checkpointed run would have.  Host file I/O,
+ * synchronous. */
+fp_status fp_checkpoint(const fp_handle *h, const char *path);
+fp_status fp_restore(fp_handle *h, const char *path);
 
 /* Operator applications on multiplier vectors of length n_lambda (after fp_factor):
  * out = F v (Eq. (3.6)), out = M^{-1} v (Eq. (3.5), scaled by W = (B B^T)^{-1} on both

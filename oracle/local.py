@@ -174,6 +174,15 @@ class LocalSystem:
                               + case.tau * (self.Af_full[self.pfree][:, self.pdir] @ pD))
         return b
 
+    def Reta_from_fields(self, u0, p0):
+        """R eta^0 = (eta_0, phi_i) for eta_0 = c0 p0 + alpha div u0 (Sec. 2.5 with Eq. 2.17) from
+        nodal fields: u0 (n_unode, 2) or flat 2 n_unode, p0 (n_pnode,), interpolated in P_k and
+        P1 on every node.  B_full = -(phi_i, div theta_j), so (div u0, phi_i) = -(B_full u0)_i."""
+        m, case = self.m, self.case
+        u = np.zeros(2 * m.n_unode) if u0 is None else np.asarray(u0, dtype=np.float64).ravel()
+        p = np.zeros(m.n_pnode) if p0 is None else np.asarray(p0, dtype=np.float64)
+        return case.c0 * (self.R_full @ p) - case.alpha * (self.B_full @ u)
+
     def Reta0(self):
         """R eta^0 for the L2 projection eta^0 of eta_0 (Sec. 2.5): the load (eta_0, phi_i)."""
         return self.eta0_load.copy()

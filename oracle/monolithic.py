@@ -34,8 +34,10 @@ class Discretization:
         return [L.Reta0() if L.m.is_poro else None for L in self.locals]
 
 
-def solve_monolithic(case, disc=None, n_steps=None, callback=None):
-    """Run the time loop; returns a list of per-step dicts with 'lambda' and 'fields'."""
+def solve_monolithic(case, disc=None, n_steps=None, callback=None, initial=None):
+    """Run the time loop; returns a list of per-step dicts with 'lambda' and 'fields'.
+    initial: optional per-subdomain (u0, p0) nodal fields (p0 None on elastic subdomains)
+    that replace the configured initial state (R eta^0 from eta_0 = c0 p0 + alpha div u0)."""
     disc = disc or Discretization(case)
     Ls, I = disc.locals, disc.iface
     K = sp.block_diag([L.K for L in Ls], format="csr")
@@ -44,6 +46,8 @@ def solve_monolithic(case, disc=None, n_steps=None, callback=None):
     lu = spla.splu(M)
     offs = np.cumsum([0] + [L.n for L in Ls])
     Reta = disc.initial_Reta()
+    if initial is not None:
+        Reta = [L.Reta_from_fields(*initial[s]) if L.m.is_poro else None for s, L in enumerate(Ls)]
     out = []
     N = case.n_steps if n_steps is None else n_steps
     for n in range(1, N + 1):

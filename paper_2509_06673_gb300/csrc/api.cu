@@ -15,6 +15,7 @@
 namespace fp {
 // kernels (defined in the other translation units)
 __global__ void k_assemble(DevTopo, DevParams, double *, double *, double *, double *);
+__global__ void k_set_initial(DevTopo, DevParams, const double *, const double *, double *);
 cudaError_t launch_csr_to_band(bool fp32, DevTopo D, const double *csr_val, void *band, int mode, cudaStream_t s);
 __global__ void k_coarse_G(DevTopo, double *, double *);
 __global__ void k_coarse_GtG(DevTopo, const double *, const double *, double *);
@@ -1415,6 +1416,32 @@ fp_status fp_assemble(fp_handle *h) {
   return FP_OK;
 }
 
+fp_status fp_set_initial(fp_handle *h, const double *u0, const double *p0) {
+  if (!h) return FP_ERR_INVALID;
+  if (h->stage < 1) { h->err = "fp_set_initial before fp_assemble"; return FP_ERR_STATE; }
+  const Topology &T = h->T;
+  const size_t nu2 = 2 * (size_t)T.unode_off[T.S], np = (size_t)T.pnode_off[T.S];
+  cudaStream_t s = h->stream;
+  // the initial fields become the reported fields until the first step
+  if (u0) CK(cudaMemcpyAsync(h->U, u0, nu2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  else CK(cudaMemsetAsync(h->U, 0, nu2 * sizeof(double), s));
+  if (p0) CK(cudaMemcpyAsync(h->PP, p0, np * sizeof(double), cudaMemcpyHostToDevice, s));
+  else CK(cudaMemsetAsync(h->PP, 0, np * sizeof(double), s));
+  CK(cudaMemsetAsync(h->XI, 0, np * sizeof(double), s));
+  CK(cudaMemsetAsync(h->ETA, 0, np * sizeof(double), s));
+  k_set_initial<<<T.S, 256, 0, s>>>(h->D, h->DP, u0 ? h->U : nullptr, p0 ? h->PP : nullptr, h->Reta);
+  CKL();
+  const int nl = std::max(T.n_lambda, 1);
+  CK(cudaMemsetAsync(h->lam_prev, 0, nl * sizeof(double), s));
+  CK(cudaMemsetAsync(h->lam_prev2, 0, nl * sizeof(double), s));
+  CK(cudaMemsetAsync(h->lam, 0, nl * sizeof(double), s));
+  CK(cudaStreamSynchronize(s));
+  h->step_n = 0;
+  h->hist = 0;
+  h->sigma_hist[0] = h->sigma_hist[1] = 0.0;
+  return FP_OK;
+}
+
 fp_status fp_factor(fp_handle *h) {
   if (!h) return FP_ERR_INVALID;
   if (h->stage < 1) { h->err = "fp_factor before fp_assemble"; return FP_ERR_STATE; }
@@ -1578,6 +1605,118 @@ fp_status fp_get_fields(const fp_handle *hc, double *u, double *xi, double *eta,
   TRY(copy_out(h, xi, h->XI, T.pnode_off[T.S] * sizeof(double), on_device));
   TRY(copy_out(h, eta, h->ETA, T.pnode_off[T.S] * sizeof(double), on_device));
   TRY(copy_out(h, p, h->PP, T.pnode_off[T.S] * sizeof(double), on_device));
+  return FP_OK;
+}
+
+fp_status fp_get_subdomain(const fp_handle *hc, int s, double *u, double *xi, double *eta, double *p,
+                           int on_device) {
+  fp_handle *h = const_cast<fp_handle *>(hc);
+  if (!h) return FP_ERR_INVALID;
+  const Topology &T = h->T;
+  if (s < 0 || s >= T.S) { h->err = "fp_get_subdomain: subdomain out of range"; return FP_ERR_INVALID; }
+  const long long u0 = T.unode_off[s], nu = T.unode_off[s + 1] - u0;
+  const long long p0 = T.pnode_off[s], np = T.pnode_off[s + 1] - p0;
+  TRY(copy_out(h, u, h->U + 2 * u0, 2 * nu * sizeof(double), on_device));
+  TRY(copy_out(h, xi, h->XI + p0, np * sizeof(double), on_device));
+  TRY(copy_out(h, eta, h->ETA + p0, np * sizeof(double), on_device));
+  TRY(copy_out(h, p, h->PP + p0, np * sizeof(double), on_device));
+  return FP_OK;
+}
+
+// ------------------------------- checkpoint / restore ----------------------------------
+// File: magic, version, the sizes that identify the topology, the host scalars of the time
+// stepping, then the device arrays in a fixed order (little-endian doubles / floats).
+namespace {
+constexpr char kCkptMagic[8] = {'F', 'E', 'T', 'I', 'P', 'E', 'C', 'K'};
+constexpr int kCkptVersion = 1;
+struct CkptHeader {
+  char magic[8];
+  int version, S, n_lambda, order_k;
+  long long nv, np, nu, nparam;
+  int step_n, hist, mlp_ready, adam_step, learned_use, pad;
+  double sigma0, sigma1;
+};
+
+struct CkptArray { void *dev; size_t bytes; };
+
+std::vector<CkptArray> ckpt_arrays(fp_handle *h) {
+  const Topology &T = h->T;
+  const size_t nl = (size_t)T.n_lambda, np = (size_t)T.pnode_off[T.S], nu = (size_t)T.unode_off[T.S];
+  return {{h->lam_prev, nl * 8}, {h->lam_prev2, nl * 8}, {h->lam, nl * 8}, {h->Reta, np * 8},
+          {h->U, 2 * nu * 8}, {h->XI, np * 8}, {h->ETA, np * 8}, {h->PP, np * 8},
+          {h->mlpP, (size_t)MLP_NPARAM * 4}, {h->mlpM1, (size_t)MLP_NPARAM * 4}, {h->mlpM2, (size_t)MLP_NPARAM * 4}};
+}
+
+CkptHeader ckpt_header(const fp_handle *h) {
+  CkptHeader c{};
+  std::memcpy(c.magic, kCkptMagic, 8);
+  c.version = kCkptVersion;
+  c.S = h->T.S; c.n_lambda = h->T.n_lambda; c.order_k = h->T.k;
+  c.nv = h->T.vec_off[h->T.S]; c.np = h->T.pnode_off[h->T.S]; c.nu = h->T.unode_off[h->T.S];
+  c.nparam = MLP_NPARAM;
+  return c;
+}
+}  // namespace
+
+fp_status fp_checkpoint(const fp_handle *hc, const char *path) {
+  fp_handle *h = const_cast<fp_handle *>(hc);
+  if (!h || !path) return FP_ERR_INVALID;
+  CkptHeader c = ckpt_header(h);
+  c.step_n = h->step_n; c.hist = h->hist; c.mlp_ready = h->mlp_ready; c.adam_step = h->adam_step;
+  c.learned_use = h->learned_use;
+  c.sigma0 = h->sigma_hist[0]; c.sigma1 = h->sigma_hist[1];
+  CK(cudaStreamSynchronize(h->stream));
+  FILE *f = std::fopen(path, "wb");
+  if (!f) { h->err = std::string("fp_checkpoint: cannot open ") + path; return FP_ERR_INVALID; }
+  bool ok = std::fwrite(&c, sizeof c, 1, f) == 1;
+  std::vector<unsigned char> buf;
+  for (const CkptArray &a : ckpt_arrays(h)) {
+    if (!ok) break;
+    buf.resize(a.bytes);
+    if (a.bytes && cudaMemcpy(buf.data(), a.dev, a.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::fclose(f);
+      h->err = "fp_checkpoint: device read failed";
+      return FP_ERR_CUDA;
+    }
+    ok = a.bytes == 0 || std::fwrite(buf.data(), 1, a.bytes, f) == a.bytes;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) { h->err = std::string("fp_checkpoint: write failed: ") + path; return FP_ERR_INVALID; }
+  return FP_OK;
+}
+
+fp_status fp_restore(fp_handle *h, const char *path) {
+  if (!h || !path) return FP_ERR_INVALID;
+  if (h->stage < 1) { h->err = "fp_restore before fp_assemble"; return FP_ERR_STATE; }
+  FILE *f = std::fopen(path, "rb");
+  if (!f) { h->err = std::string("fp_restore: cannot open ") + path; return FP_ERR_INVALID; }
+  CkptHeader c{};
+  const CkptHeader want = ckpt_header(h);
+  if (std::fread(&c, sizeof c, 1, f) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != kCkptVersion ||
+      c.S != want.S || c.n_lambda != want.n_lambda || c.order_k != want.order_k || c.nv != want.nv ||
+      c.np != want.np || c.nu != want.nu || c.nparam != want.nparam) {
+    std::fclose(f);
+    h->err = "fp_restore: not a checkpoint of this problem (magic, version or sizes differ)";
+    return FP_ERR_INVALID;
+  }
+  std::vector<std::vector<unsigned char>> data;
+  for (const CkptArray &a : ckpt_arrays(h)) {
+    data.emplace_back(a.bytes);
+    if (a.bytes && std::fread(data.back().data(), 1, a.bytes, f) != a.bytes) {
+      std::fclose(f);
+      h->err = "fp_restore: file truncated";
+      return FP_ERR_INVALID;
+    }
+  }
+  std::fclose(f);
+  const auto arrays = ckpt_arrays(h);
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < arrays.size(); ++i)
+    if (arrays[i].bytes) CK(cudaMemcpy(arrays[i].dev, data[i].data(), arrays[i].bytes, cudaMemcpyHostToDevice));
+  h->step_n = c.step_n; h->hist = c.hist; h->mlp_ready = c.mlp_ready; h->adam_step = c.adam_step;
+  h->learned_use = c.learned_use;
+  h->sigma_hist[0] = c.sigma0; h->sigma_hist[1] = c.sigma1;
+  h->gdirty = 1;
   return FP_OK;
 }
 

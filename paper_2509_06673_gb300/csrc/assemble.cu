@@ -248,6 +248,68 @@ __global__ void k_assemble(DevTopo T, DevParams P, double *csr_val, double *fsta
   }
 }
 
+// R eta^0 from given initial fields (Sec. 2.5, eta_0 = c0 p_0 + alpha div u_0 by Eq. 2.17):
+// Reta[v] = sum over elements of int (c0 p0_h + alpha div u0_h) phi_v, with u0_h the P_k
+// interpolant of the nodal u0 (every node, Dirichlet ones included) and p0_h the P1
+// interpolant of p0; the integrand has degree <= 2, so the edge-midpoint rule is exact.
+// u0, p0: canonical node arrays (may be null: zero).  One CTA per poroelastic subdomain,
+// cells in 4 colours as in the assembly (race-free, fixed order).
+__global__ void k_set_initial(DevTopo T, DevParams P, const double *u0, const double *p0, double *Reta) {
+  const int s = blockIdx.x;
+  const DevTpl t = T.tpl[T.sub_tpl[s]];
+  const long long pn0 = T.pnode_off[s], un0 = T.unode_off[s];
+  for (int v = threadIdx.x; v < t.npx * t.npy; v += blockDim.x) Reta[pn0 + v] = 0.0;
+  __syncthreads();
+  if (!t.poro) return;
+  const int k = t.k, nun = k == 1 ? 3 : 6, nx = t.nx, ny = t.ny;
+  const double hx = T.sub_hx[s], hy = T.sub_hy[s];
+  const double Lq[3][3] = {{0.5, 0.5, 0.0}, {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}};
+  for (int color = 0; color < 4; ++color) {
+    const int ci = color & 1, cj = color >> 1;
+    const int ncx = (nx - ci + 1) / 2, ncy = (ny - cj + 1) / 2;
+    for (int cell = threadIdx.x; cell < ncx * ncy; cell += blockDim.x) {
+      const int i = ci + 2 * (cell % ncx), j = cj + 2 * (cell / ncx);
+      for (int tt = 0; tt < 2; ++tt) {
+        double vv[3][2], G[3][2], area;
+        tri_vertices(tt, hx, hy, vv);
+        bary_grad(vv, G, area);
+        // vertex offsets in cell units: type 0 (0,0),(1,0),(1,1); type 1 (0,0),(1,1),(0,1)
+        const int ox[3] = {0, 1, tt == 0 ? 1 : 0}, oy[3] = {0, tt == 0 ? 0 : 1, 1};
+        // P1 vertices (pressure grid) and P_k nodes (displacement grid, x fastest)
+        int pv[3], un[6];
+        for (int a = 0; a < 3; ++a) {
+          pv[a] = (j + oy[a]) * t.npx + (i + ox[a]);
+          un[a] = (k * (j + oy[a])) * t.nux + k * (i + ox[a]);
+        }
+        if (k == 2) {
+          const int ea[3] = {0, 1, 2}, eb[3] = {1, 2, 0};
+          for (int m = 0; m < 3; ++m) {
+            const int gx = (2 * (i + ox[ea[m]]) + 2 * (i + ox[eb[m]])) / 2;
+            const int gy = (2 * (j + oy[ea[m]]) + 2 * (j + oy[eb[m]])) / 2;
+            un[3 + m] = gy * t.nux + gx;
+          }
+        }
+        double El[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < 3; ++q) {
+          double pq = 0.0, div = 0.0;
+          if (p0)
+            for (int a = 0; a < 3; ++a) pq += Lq[q][a] * p0[pn0 + pv[a]];
+          if (u0)
+            for (int a = 0; a < nun; ++a) {
+              double g[2];
+              grad_phi(k, a, Lq[q], G, g);
+              div += g[0] * u0[2 * (un0 + un[a])] + g[1] * u0[2 * (un0 + un[a]) + 1];
+            }
+          const double eta = P.c0 * pq + P.alpha * div;
+          for (int m = 0; m < 3; ++m) El[m] += area / 3.0 * eta * Lq[q][m];
+        }
+        for (int m = 0; m < 3; ++m) Reta[pn0 + pv[m]] += El[m];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Band matrix (cyclic column layout, see band.cu) from the CSR values.  mode 0: Neumann
 // (identity rows on the fixed dofs of floating subdomains); mode 1: Dirichlet (identity rows
 // on every dof touched by B_s).  One CTA per subdomain.

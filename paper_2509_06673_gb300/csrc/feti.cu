@@ -442,6 +442,13 @@ __global__ void k_recover(DevTopo D, DevParams P, const double *xf, const double
   const double hx = D.sub_hx[s], hy = D.sub_hy[s];
   const double xc = D.sub_x0[s] + 0.5 * t.nx * hx, yc = D.sub_y0[s] + 0.5 * t.ny * hy;
   const double L = fmax(t.nx * hx, t.ny * hy);
+  // Dirichlet nodes carry the (homogeneous) boundary data: zero everything first
+  for (int i = threadIdx.x; i < 2 * t.nux * t.nuy; i += blockDim.x) U[2 * un0 + i] = 0.0;
+  for (int i = threadIdx.x; i < t.npx * t.npy; i += blockDim.x) {
+    XI[pn0 + i] = 0.0;
+    PP[pn0 + i] = 0.0;
+  }
+  __syncthreads();
   for (int d = threadIdx.x; d < t.n; d += blockDim.x) {
     const int f = dfield[d], node = dnode[d];
     double v = a[d] - b[d];

@@ -28,7 +28,8 @@ FP_PREC_FP64, FP_PREC_MIXED = 0, 1
 FP_PRECOND_DIRICHLET, FP_PRECOND_NONE = 0, 2
 
 EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_get_sizes",
-            "fp_get_lambda", "fp_get_lambda_keys", "fp_get_fields", "fp_apply_F",
+            "fp_get_lambda", "fp_get_lambda_keys", "fp_get_fields", "fp_get_subdomain", "fp_set_initial",
+            "fp_checkpoint", "fp_restore", "fp_apply_F",
             "fp_apply_precond", "fp_apply_projection", "fp_apply_projection_noalloc",
             "fp_get_dof_map",
             "fp_get_local_matrix", "fp_get_step_timing", "fp_set_option", "fp_set_profiling",
@@ -91,6 +92,10 @@ _lib.fp_get_sizes.argtypes = [_vp, ctypes.POINTER(Sizes)]
 _lib.fp_get_lambda.argtypes = [_vp, _vp, ctypes.c_int]
 _lib.fp_get_lambda_keys.argtypes = [_vp, _vp]
 _lib.fp_get_fields.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.fp_get_subdomain.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.fp_checkpoint.argtypes = [_vp, ctypes.c_char_p]
+_lib.fp_set_initial.argtypes = [_vp, _vp, _vp]
+_lib.fp_restore.argtypes = [_vp, ctypes.c_char_p]
 for _n in ("fp_apply_F", "fp_apply_precond", "fp_apply_projection"):
     getattr(_lib, _n).argtypes = [_vp, _vp, _vp, ctypes.c_int]
 _lib.fp_apply_projection_noalloc.argtypes = [_vp, _vp, _vp]
@@ -222,6 +227,32 @@ class Solver:
         self._check(_lib.fp_get_fields(self._h, u.ctypes.data, xi.ctypes.data, eta.ctypes.data,
                                        p.ctypes.data, 0))
         return u, xi, eta, p
+
+    def get_subdomain(self, s):
+        """(u, xi, eta, p) of subdomain s, u as an (n_unode, 2) array (same as split_fields)."""
+        c = self.case
+        k = c.order_k
+        if not 0 <= s < c.nsub:   # the library reports the bad index
+            self._check(_lib.fp_get_subdomain(self._h, int(s), None, None, None, None, 0))
+        nx, ny = c.cells_x[s % c.nsub_x], c.cells_y[s // c.nsub_x]
+        u = np.empty(2 * (k * nx + 1) * (k * ny + 1))
+        xi, eta, p = (np.empty((nx + 1) * (ny + 1)) for _ in range(3))
+        self._check(_lib.fp_get_subdomain(self._h, int(s), u.ctypes.data, xi.ctypes.data, eta.ctypes.data,
+                                          p.ctypes.data, 0))
+        return u.reshape(-1, 2), xi, eta, p
+
+    def set_initial(self, u0=None, p0=None):
+        """Initial nodal fields in the layout of get_fields (None: zero)."""
+        u = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+        p = None if p0 is None else np.ascontiguousarray(p0, dtype=np.float64)
+        self._check(_lib.fp_set_initial(self._h, None if u is None else u.ctypes.data,
+                                        None if p is None else p.ctypes.data))
+
+    def checkpoint(self, path):
+        self._check(_lib.fp_checkpoint(self._h, str(path).encode()))
+
+    def restore(self, path):
+        self._check(_lib.fp_restore(self._h, str(path).encode()))
 
     def _op(self, fn, v):
         v = np.ascontiguousarray(v, dtype=np.float64)
