@@ -192,6 +192,8 @@ def run_native(args):
         torch.distributed.barrier()
     from paper_2509_06673_gb300 import fetipe as F
     case = workload(args.config, args.precision)
+    if args.precond:
+        case = case.with_(precond=args.precond)
     stream = torch.cuda.current_stream()
     sol = F.Solver(case, stream=stream.cuda_stream)
     for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
@@ -310,6 +312,7 @@ def run_native(args):
                        % (s.factor_bytes / 1e9), "setup_s": setup_s, "pcg_iterations": its, "pcg_restarts": restarts,
                        "pcg_stagnation_stops": stags, "autotuned": tuning,
                        "graph": args.graph != 0, "explicit_operators": bool(args.explicit),
+                       "preconditioner": {0: "dirichlet", 1: "lumped", 2: "none"}.get(tuning["precond"]),
                        "learned_lambda0": learned,
                        "learned_guess_chosen": wins if learned else None,
                        "guess_rel_residual_prev_learned": gres if learned else None,
@@ -379,6 +382,8 @@ def main():
     ap.add_argument("--factor-fp64", type=int, default=None, help="mixed: factor in FP64, round to FP32")
     ap.add_argument("--factor-nb", type=int, default=None, help="panel width of the factorisation")
     ap.add_argument("--explicit", type=int, default=1, help="1: explicit local interface operators")
+    ap.add_argument("--precond", default=None, choices=[None, "dirichlet", "lumped", "auto"],
+                    help="preconditioner (both arms); default: the workload's (Dirichlet)")
     ap.add_argument("--fp64-explicit", type=int, default=1, help="explicit operators in the FP64 arm")
     ap.add_argument("--graph", type=int, default=None, help="1: one CUDA graph launch per time step")
     ap.add_argument("--learned", type=int, default=1, help="mixed arm: learned lambda_0 (trained in warm-up)")

@@ -46,7 +46,12 @@ typedef enum {
 
 enum { FP_SOURCE_MANUFACTURED = 0, FP_SOURCE_POINT = 1, FP_SOURCE_MANUFACTURED_T = 2 };
 enum { FP_PREC_FP64 = 0, FP_PREC_MIXED = 1 };
-enum { FP_PRECOND_DIRICHLET = 0, FP_PRECOND_NONE = 2 };
+/* Preconditioner: DIRICHLET W B S B^T W (Eq. (3.5)); LUMPED W B K_bb B^T W, the interface
+ * block of the local 3-field matrices in place of their Schur complement (Sec. 3.3: the M_A
+ * of Algorithm 2 reduces to it), no local solve; NONE; AUTO: fp_factor times probe runs of
+ * Algorithm 1 with DIRICHLET and LUMPED and keeps the one with the smaller predicted time
+ * to the tolerance (see fp_get_tuning). */
+enum { FP_PRECOND_DIRICHLET = 0, FP_PRECOND_LUMPED = 1, FP_PRECOND_NONE = 2, FP_PRECOND_AUTO = 3 };
 
 /*
  * Partition and mesh (Sec. 2.4; Sec. 4.1 uses uniform triangulations).  The unit square is
@@ -293,6 +298,8 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *                       refined band solves).  The right-hand side and the recovery keep full
  *                       band solves.  Needs b + 64 window rows of 32 values in shared memory
  *                       (FP_ERR_INVALID when the band is too wide).  Takes effect at fp_factor.
+ *   "explicit_tile" [0] right-hand sides per task of the explicit-operator build: 32 or 16
+ *                       (0: 32 where its shared-memory window fits, else 16)
  *   "autotune"     [1]  fp_factor times candidate launch shapes on the handle's own factors
  *                       and keeps the fastest (see fp_get_tuning); explicitly set shape
  *                       options are kept fixed.  Takes effect at the next fp_factor.
@@ -342,6 +349,11 @@ typedef struct {
   double factor_ms, solve_ms;
   int candidates;
   double explicit_ms;  /* build time of the explicit interface operators (0: not built) */
+  int precond;         /* preconditioner in use (FP_PRECOND_*; the AUTO choice) */
+  /* AUTO probes (index 0 DIRICHLET, 1 LUMPED; zero when not probed): contraction of the
+   * residual norm per iteration over 30 iterations of Algorithm 1 on a seeded random
+   * right-hand side in range(P) from lambda_0 = 0, and the time per iteration */
+  double precond_rate[2], precond_ms_per_it[2];
 } fp_tuning;
 fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out);
 

@@ -127,8 +127,13 @@ def minres(apply_A, apply_Minv, b_res, x0, tol, ref, max_it):
 
 
 class FETI:
-    def __init__(self, case, disc=None, fixed_override=None):
+    def __init__(self, case, disc=None, fixed_override=None, precond=None):
         self.case = case
+        # "dirichlet" (Eq. (3.5)), "lumped" (Sec. 3.3: the M_A of Algorithm 2, which reduces to
+        # the local matrices' interface block K_bb) or "none"
+        self.precond_kind = precond or getattr(case, "precond", "dirichlet")
+        if self.precond_kind not in ("dirichlet", "lumped", "none"):
+            self.precond_kind = "dirichlet"
         self.disc = disc or Discretization(case)
         Ls, I = self.disc.locals, self.disc.iface
         self.Ls, self.I = Ls, I
@@ -144,6 +149,7 @@ class FETI:
             self.lu.append(spla.splu(L.K[keep][:, keep].tocsc()))
         # Dirichlet data ---------------------------------------------------------------
         self.bd, self.bu_mask, self.dlu, self.Kbb, self.Kbi, self.Kib = [], [], [], [], [], []
+        self.Kbb3 = []
         for s, L in enumerate(Ls):
             Bs = I.Bs[s].tocsc()
             bd = np.flatnonzero(np.diff(Bs.indptr))
@@ -156,6 +162,15 @@ class FETI:
             self.Kbb.append(K[bd][:, bd])
             self.Kbi.append(K[bd][:, idof])
             self.Kib.append(K[idof][:, bd])
+            # interface block of the 3-field local matrix (eta eliminated, the library's local
+            # system): the 4-field K_bb plus -(c0 + alpha^2 / lambda) R on the pressure dofs
+            Kb3 = K[bd][:, bd].toarray()
+            if L.m.is_poro and is_pdof.any():
+                ip = np.flatnonzero(is_pdof)
+                nodes = L.pfree[bd[ip] - L.off_p]
+                c = case.c0 + case.alpha ** 2 / case.lame_lambda
+                Kb3[np.ix_(ip, ip)] -= c * L.R_full[nodes][:, nodes].toarray()
+            self.Kbb3.append(Kb3)
         # coarse -----------------------------------------------------------------------
         self.nc = I.G.shape[1]
         self.GtG_cho = sla.cho_factor(I.GtG) if self.nc else None
@@ -180,9 +195,19 @@ class FETI:
             y -= self.Kbi[s] @ self.dlu[s].solve(self.Kib[s] @ xb)
         return y
 
+    def local_precond(self, s, xb):
+        """The local operator of the preconditioner on the interface dofs of s: the Dirichlet
+        Schur complement S_s, or the lumped interface block K_bb of the 3-field matrix."""
+        if self.precond_kind == "lumped":
+            return self.Kbb3[s] @ xb
+        return self.S_apply(s, xb)
+
     def precond(self, r, block=False):
-        """W sum_s B_s S^_s B_s^T W r with S^_s = S_s (Eq. (3.5)), or with ``block`` the
-        positive definite diag(S_uu, -S_pp) used by MINRES."""
+        """W sum_s B_s S^_s B_s^T W r with S^_s = S_s (Eq. (3.5); K_bb for the lumped
+        preconditioner), or with ``block`` the positive definite diag(S_uu, -S_pp) used by
+        MINRES.  The identity for precond "none"."""
+        if self.precond_kind == "none":
+            return np.array(r, dtype=np.float64)
         I = self.I
         rw = I.apply_W(r)
         out = np.zeros(I.n_lambda)
@@ -193,11 +218,11 @@ class FETI:
             yb = (B.T @ rw)[bd]
             um = self.bu_mask[s]
             if block and (~um).any():
-                zu = self.S_apply(s, np.where(um, yb, 0.0))
-                zp = self.S_apply(s, np.where(um, 0.0, yb))
+                zu = self.local_precond(s, np.where(um, yb, 0.0))
+                zp = self.local_precond(s, np.where(um, 0.0, yb))
                 zb = np.where(um, zu, -zp)
             else:
-                zb = self.S_apply(s, yb)
+                zb = self.local_precond(s, yb)
             full = np.zeros(self.Ls[s].n)
             full[bd] = zb
             out += B @ full

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 #include <functional>
+#include <random>
 #include <vector>
 
 #include "device.cuh"
@@ -29,12 +30,12 @@ cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int ch
 cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
                              cudaStream_t stream);
 cudaError_t launch_round_to_float(const double *src, float *dst, long long n, cudaStream_t stream);
-size_t mrhs_smem_bytes(bool fp32, int R, int LDp);
-cudaError_t launch_band_mrhs(bool fp32, int nr, int grid, cudaStream_t st, const int *task_s, const int *task_j0,
-                             int ntask, DevTopo D, const void *fac, const void *linv, const long long *linv_off,
-                             const double *csr, int kind, void *scratch, long long sstride, int *counter, void *out,
-                             const long long *out_off, int R, int LDp);
-int mrhs_blocks_per_sm(bool fp32, int nr, int R, int LDp);
+size_t mrhs_smem_bytes(bool fp32, int R, int LDp, int mt);
+cudaError_t launch_band_mrhs(bool fp32, int bmax, int mt, int grid, cudaStream_t st, const int *task_s,
+                             const int *task_j0, int ntask, DevTopo D, const void *fac, const void *linv,
+                             const long long *linv_off, const double *csr, int kind, void *scratch, long long sstride,
+                             int *counter, void *out, const long long *out_off, int R, int LDp);
+int mrhs_blocks_per_sm(bool fp32, int bmax, int mt, int R, int LDp);
 cudaError_t launch_explicit_apply(bool fp32, DevTopo D, int S, int mmax_bnd, const void *ops, const long long *op_off,
                                   double *xloc, const int *fl, cudaStream_t st);
 cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, const long long *full_off,
@@ -129,14 +130,16 @@ struct fp_handle {
   SolveShape shape{0, 0, 0};  // launch shape of the blocked solves (set at fp_factor)
   fp_tuning tuning{};
   // explicit local interface operators F_s, S_s (dense, per subdomain; option "explicit")
+  int precond_req = 0;      // requested preconditioner (FP_PRECOND_AUTO resolved at fp_factor)
   int explicit_ops = 0, ops_ready = 0, opF64_ready = 0;
+  int explicit_tile = 0;    // right-hand sides per build task: 0 automatic (32, else 16)
   // the PCG loop's operators: FP64 full m x mp matrices (FP64), FP32 upper 32 x 32 tiles (mixed)
   void *opF = nullptr, *opS = nullptr;
   double *opF64 = nullptr;              // mixed precision: F_s in FP64 for the accurate applies
   const long long *op_off = nullptr, *tile_off = nullptr, *linv_off_dev = nullptr;
   long long op_total = 0, tile_total = 0;
-  const int *mrhs_s = nullptr, *mrhs_j0 = nullptr;
-  int mrhs_ntask = 0;
+  const int *mrhs_s[2] = {}, *mrhs_j0[2] = {};  // build tasks for tiles of 32 / 16 right-hand sides
+  int mrhs_ntask[2] = {0, 0};
   double explicit_build_ms = 0;
   int factor_fp64 = 1;     // mixed precision: factor in FP64, round the finished factor to FP32
   double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
@@ -341,23 +344,26 @@ fp_status build_device(fp_handle *h) {
     // explicit-operator layout (rows padded to a multiple of 4) and build tasks: every
     // subdomain in cost order, tiles of 32 right-hand sides
     std::vector<long long> ooff(T.S + 1, 0), toff(T.S + 1, 0);
-    std::vector<int> ms, mj;
+    std::vector<int> ms[2], mj[2];
     for (int s = 0; s < T.S; ++s) {
       const long long m = (long long)T.tpl[T.sub_tpl[s]].bnd.size(), nt = (m + 31) / 32;
       ooff[s + 1] = ooff[s] + m * ((m + 3) & ~3LL);
       toff[s + 1] = toff[s] + nt * (nt + 1) / 2 * 1024;
     }
-    for (int s : order) {
-      const int m = (int)T.tpl[T.sub_tpl[s]].bnd.size();
-      for (int j0 = 0; j0 < m; j0 += 32) { ms.push_back(s); mj.push_back(j0); }
-    }
+    for (int w = 0; w < 2; ++w)
+      for (int s : order) {
+        const int m = (int)T.tpl[T.sub_tpl[s]].bnd.size();
+        for (int j0 = 0; j0 < m; j0 += (w == 0 ? 32 : 16)) { ms[w].push_back(s); mj[w].push_back(j0); }
+      }
     h->op_total = ooff[T.S];
     h->tile_total = toff[T.S];
-    h->mrhs_ntask = (int)ms.size();
     TRY(upload(h, &h->op_off, ooff));
     TRY(upload(h, &h->tile_off, toff));
-    TRY(upload(h, &h->mrhs_s, ms));
-    TRY(upload(h, &h->mrhs_j0, mj));
+    for (int w = 0; w < 2; ++w) {
+      h->mrhs_ntask[w] = (int)ms[w].size();
+      TRY(upload(h, &h->mrhs_s[w], ms[w]));
+      TRY(upload(h, &h->mrhs_j0[w], mj[w]));
+    }
   }
   std::vector<BandTask> tk;
   int mmax = 1;
@@ -650,6 +656,8 @@ fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, boo
   return FP_OK;
 }
 
+fp_status apply_M_lumped(fp_handle *h, const double *v, double *out, const int *fl);
+
 // out = W B S B^T W v  (Eq. (3.5) with the scaling W)
 fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
   const int nl = h->T.n_lambda;
@@ -658,6 +666,7 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
     if (out != v) CK(cudaMemcpyAsync(out, v, nl * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     return FP_OK;
   }
+  if (h->P.precond == FP_PRECOND_LUMPED) return apply_M_lumped(h, v, out, fl);
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
   k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl);
   CKL();
@@ -673,6 +682,21 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
     TRY(solve_local(h, true, h->XY, fl));
     k_bnd_apply<<<h->T.S, 256, h->nbnd_max * sizeof(double), h->stream>>>(h->D, h->csr_val, h->XY, h->XP, fl);
   }
+  CKL();
+  k_gather<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, h->t2, fl);
+  k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, h->t2, out, fl);
+  CKL();
+  return FP_OK;
+}
+
+// out = W B K_bb B^T W v: the lumped preconditioner (Sec. 3.3), the local matrices' interface
+// block in place of the Schur complement (no local solve)
+fp_status apply_M_lumped(fp_handle *h, const double *v, double *out, const int *fl) {
+  const int nl = h->T.n_lambda;
+  const int ng = (int)h->T.wgrp_first.size();
+  k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
+  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl);
+  k_bnd_apply<<<h->T.S, 256, h->nbnd_max * sizeof(double), h->stream>>>(h->D, h->csr_val, nullptr, h->XP, fl);
   k_gather<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, h->t2, fl);
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, h->t2, out, fl);
   CKL();
@@ -953,23 +977,26 @@ fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, i
   const size_t esz = fp32 ? 4 : 8;
   int bmax = 0, nmax = 0;
   for (const Template &t : h->T.tpl) { bmax = std::max(bmax, t.b); nmax = std::max(nmax, t.n); }
-  const int R = (bmax + 64 + 31) / 32 * 32, LDp = h->ldmax + 4, nr = (bmax + 31) / 32;
-  if (nr > 16 || mrhs_smem_bytes(fp32, R, LDp) > 227 * 1024) {
+  const int R = (bmax + 64 + 31) / 32 * 32, LDp = h->ldmax + 4;
+  // tiles of 32 right-hand sides, or 16 where the 32-wide window does not fit
+  int mt = 32, w = 0;
+  int bps = h->explicit_tile == 16 ? 0 : mrhs_blocks_per_sm(fp32, bmax, 32, R, LDp);
+  if (bps < 1 && h->explicit_tile != 32) { mt = 16; w = 1; bps = mrhs_blocks_per_sm(fp32, bmax, 16, R, LDp); }
+  if (bps < 1) {
     h->err = "explicit operators: the band is too wide for the shared-memory window";
     return FP_ERR_INVALID;
   }
-  const int bps = mrhs_blocks_per_sm(fp32, nr, R, LDp);
-  if (bps < 1) { h->err = "explicit operators: build kernel cannot be resident"; return FP_ERR_CUDA; }
-  const int grid = std::min(bps * h->num_sms, std::max(1, h->mrhs_ntask));
+  const int grid = std::min(bps * h->num_sms, std::max(1, h->mrhs_ntask[w]));
   CK(cudaMemsetAsync(out, 0, (size_t)h->op_total * esz, h->stream));
-  const long long sstride = (long long)nmax * 32;
+  const long long sstride = (long long)nmax * mt;
   void *scratch = nullptr;
   CK(cudaMalloc(&scratch, (size_t)grid * sstride * esz));
   CK(cudaEventRecord(h->ev[4], h->stream));
   cudaError_t e = cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
-    e = launch_band_mrhs(fp32, nr, grid, h->stream, h->mrhs_s, h->mrhs_j0, h->mrhs_ntask, h->D, fac, linv,
-                         h->linv_off_dev, h->csr_val, kind, scratch, sstride, h->counter, out, h->op_off, R, LDp);
+    e = launch_band_mrhs(fp32, bmax, mt, grid, h->stream, h->mrhs_s[w], h->mrhs_j0[w], h->mrhs_ntask[w], h->D, fac,
+                         linv, h->linv_off_dev, h->csr_val, kind, scratch, sstride, h->counter, out, h->op_off, R,
+                         LDp);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev[5], h->stream);
   const cudaError_t es = cudaStreamSynchronize(h->stream);
   cudaFree(scratch);
@@ -993,16 +1020,19 @@ fp_status alloc_op(fp_handle *h, void **p, size_t bytes) {
 // F_s is the FP64 one of the factorisation rounded when it exists, else formed in FP32;
 // S_s is formed in FP32 from the FP32 Dirichlet factors.
 fp_status build_explicit(fp_handle *h) {
+  const bool need_S = h->precond_req == FP_PRECOND_DIRICHLET || h->precond_req == FP_PRECOND_AUTO;
   if (h->P.precision == FP_PREC_FP64) {
     TRY(alloc_op(h, &h->opF, (size_t)h->op_total * 8));
-    TRY(alloc_op(h, &h->opS, (size_t)h->op_total * 8));
     TRY(run_mrhs(h, false, h->facN, h->linvN, 0, h->opF));
-    TRY(run_mrhs(h, false, h->facD, h->linvD, 1, h->opS));
+    if (need_S) {
+      TRY(alloc_op(h, &h->opS, (size_t)h->op_total * 8));
+      TRY(run_mrhs(h, false, h->facD, h->linvD, 1, h->opS));
+    }
     h->ops_ready = 1;
     return FP_OK;
   }
   TRY(alloc_op(h, &h->opF, (size_t)h->tile_total * 4));
-  TRY(alloc_op(h, &h->opS, (size_t)h->tile_total * 4));
+  if (need_S) TRY(alloc_op(h, &h->opS, (size_t)h->tile_total * 4));
   void *full = nullptr;
   CK(cudaMalloc(&full, (size_t)h->op_total * 4));
   fp_status st = FP_OK;
@@ -1011,14 +1041,86 @@ fp_status build_explicit(fp_handle *h) {
     if (st == FP_OK && launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opF, h->tile_off,
                                        h->stream) != cudaSuccess) { h->err = "pack"; st = FP_ERR_CUDA; }
   }
-  if (st == FP_OK) st = run_mrhs(h, true, h->facD, h->linvD, 1, full);
-  if (st == FP_OK && launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opS, h->tile_off,
-                                     h->stream) != cudaSuccess) { h->err = "pack"; st = FP_ERR_CUDA; }
+  if (st == FP_OK && need_S) st = run_mrhs(h, true, h->facD, h->linvD, 1, full);
+  if (st == FP_OK && need_S &&
+      launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opS, h->tile_off, h->stream) != cudaSuccess) {
+    h->err = "pack";
+    st = FP_ERR_CUDA;
+  }
   const cudaError_t e = cudaStreamSynchronize(h->stream);
   cudaFree(full);
   if (st != FP_OK) return st;
   if (e != cudaSuccess) { h->err = cudaGetErrorString(e); return FP_ERR_CUDA; }
   h->ops_ready = 1;
+  return FP_OK;
+}
+
+// ------------------------------ preconditioner autotuning ------------------------------
+// A probe run of Algorithm 1 with preconditioner pc: 30 iterations from lambda_0 = 0 on a
+// seeded random right-hand side in range(P) (no stop test); returns the contraction of the
+// residual norm per iteration and the time per iteration.  Uses only step scratch vectors.
+fp_status pcg_start(fp_handle *h);
+fp_status pcg_iteration(fp_handle *h);
+
+fp_status probe_precond(fp_handle *h, int pc, double *rho, double *ms_it) {
+  const int nl = h->T.n_lambda, N = 30;
+  cudaStream_t s = h->stream;
+  h->P.precond = pc;
+  std::vector<double> v(nl);
+  std::mt19937_64 gen(0x5eed5eedULL);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (double &x : v) x = nd(gen);
+  CK(cudaMemcpyAsync(h->t2, v.data(), nl * sizeof(double), cudaMemcpyHostToDevice, s));
+  TRY(apply_P(h, h->t2, h->r, h->fl_zero));
+  CK(cudaMemsetAsync(h->lam, 0, nl * sizeof(double), s));
+  int hfl[FL_N] = {};
+  hfl[FL_MAXIT] = N + 1;
+  CK(cudaMemcpyAsync(h->fl, hfl, sizeof hfl, cudaMemcpyHostToDevice, s));
+  const double zero = 0.0, one = 1.0;
+  CK(cudaMemcpyAsync(h->sc + SC_TOL2, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->sc + SC_REF2, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  TRY(dot(h, h->r, h->r, OP_STORE, h->nrm, nullptr));
+  CK(cudaEventRecord(h->ev[4], s));
+  TRY(pcg_start(h));
+  for (int i = 0; i < N; ++i) TRY(pcg_iteration(h));
+  CK(cudaEventRecord(h->ev[5], s));
+  double r0 = 0.0;
+  CK(cudaMemcpyAsync(&r0, h->nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]));
+  const int its = h->h_fl[FL_ITER];
+  const double r1 = h->h_sc[SC_RNORM2];
+  *ms_it = its > 0 ? ms / its : 1e30;
+  *rho = (its > 0 && !h->h_fl[FL_STATUS] && r0 > 0 && r1 == r1) ? std::pow(r1 / r0, 0.5 / its) : 1.0;
+  return FP_OK;
+}
+
+// FP_PRECOND_AUTO: probe DIRICHLET and LUMPED, keep the smaller predicted time to the
+// tolerance, log(tol) / log(rho) iterations at the measured time per iteration
+fp_status autotune_precond(fp_handle *h) {
+  h->tuning.precond_rate[0] = h->tuning.precond_rate[1] = 0.0;
+  h->tuning.precond_ms_per_it[0] = h->tuning.precond_ms_per_it[1] = 0.0;
+  if (h->precond_req != FP_PRECOND_AUTO) {
+    h->P.precond = h->precond_req;
+    h->tuning.precond = h->P.precond;
+    return FP_OK;
+  }
+  const int cand[2] = {FP_PRECOND_DIRICHLET, FP_PRECOND_LUMPED};
+  double best = 1e300;
+  int pick = FP_PRECOND_DIRICHLET;
+  for (int c = 0; c < 2; ++c) {
+    double rho = 1.0, msi = 0.0;
+    TRY(probe_precond(h, cand[c], &rho, &msi));
+    h->tuning.precond_rate[c] = rho;
+    h->tuning.precond_ms_per_it[c] = msi;
+    const double its = rho > 0.0 && rho < 1.0 ? std::log(h->P.tol) / std::log(rho) : 1e300;
+    if (its * msi < best) { best = its * msi; pick = cand[c]; }
+  }
+  h->P.precond = pick;
+  h->tuning.precond = pick;
   return FP_OK;
 }
 
@@ -1349,10 +1451,12 @@ fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cud
   if (!h) return FP_ERR_OOM;
   if (!params || !mesh) { delete h; return FP_ERR_INVALID; }
   h->P = *params;
+  h->precond_req = h->P.precond;
+  if (h->P.precond == FP_PRECOND_AUTO) h->P.precond = FP_PRECOND_DIRICHLET;
   if (!(h->P.lame_lambda > 0) || !(h->P.mu > 0) || !(h->P.c0 > 0) || !(h->P.tau > 0) || !(h->P.mu_f > 0) ||
       !(h->P.alpha >= 0) || !(h->P.tol > 0) || h->P.max_it < 1 ||
       (h->P.precision != FP_PREC_FP64 && h->P.precision != FP_PREC_MIXED) ||
-      (h->P.precond != FP_PRECOND_DIRICHLET && h->P.precond != FP_PRECOND_NONE)) {
+      h->P.precond < FP_PRECOND_DIRICHLET || h->P.precond > FP_PRECOND_AUTO) {
     g_create_err = "fp_create: invalid parameters";
     delete h;
     return FP_ERR_INVALID;
@@ -1458,6 +1562,8 @@ fp_status fp_factor(fp_handle *h) {
     TRY(build_explicit(h));
     TRY(check_status(h));
   }
+  TRY(autotune_precond(h));
+  TRY(check_status(h));
   h->stage = 2;
   h->gdirty = 1;
   return FP_OK;
@@ -1927,6 +2033,7 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "solve_cps") { if (v < 0 || v > 2) return bad(); h->solve_cps = v; }
   else if (k == "factor_nb") { if (v != 0 && (v < 4 || v > 64 || v % 4)) return bad(); h->factor_nb = v; }
   else if (k == "explicit") { if (v < 0 || v > 1) return bad(); h->explicit_ops = v; }
+  else if (k == "explicit_tile") { if (v != 0 && v != 16 && v != 32) return bad(); h->explicit_tile = v; }
   else if (k == "autotune") { if (v < 0 || v > 1) return bad(); h->autotune = v; }
   else { h->err = "fp_set_option: unknown key " + k; return FP_ERR_INVALID; }
   h->gdirty = 1;

@@ -19,8 +19,6 @@
 
 namespace fp {
 
-constexpr int MRHS_T = 32;  // right-hand sides per task
-
 template <typename T>
 __device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
   v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
@@ -28,20 +26,24 @@ __device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
 
 // kind 0: F_s (right-hand sides e_{b_j}; fixed dofs of floating subdomains give zero
 // columns), kind 1: S_s (right-hand sides -K_{i, b_j} on interior rows, Dirichlet factor).
-// Task t = (subdomain task_s[t], first column task_j0[t]).
-template <typename T, int NR>
+// Task t = (subdomain task_s[t], first column task_j0[t]); MT right-hand sides per task
+// (32, or 16 where a 32-wide window does not fit in shared memory).  Thread layout: CG = MT/4
+// column groups of 4, RG = 256/CG row groups; NR = ceil(b / RG) rows per thread in the
+// forward coupling; only the first 32 row groups work on the 32-row diagonal blocks.
+template <typename T, int NR, int MT>
 __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int *task_j0, int ntask, DevTopo D,
                                                    const T *fac, const T *linv, const long long *linv_off,
                                                    const double *csr_val, int kind, T *scratch,
                                                    long long scratch_stride, int *counter, T *out,
                                                    const long long *out_off, int R, int LDp) {
+  constexpr int CG = MT / 4, RG = 256 / CG;
   extern __shared__ unsigned char smraw[];
   T *Wn = reinterpret_cast<T *>(smraw);  // R x MT window
-  T *Fc = Wn + (size_t)R * MRHS_T;       // 32 x LDp staged factor columns
+  T *Fc = Wn + (size_t)R * MT;           // 32 x LDp staged factor columns
   T *Lv = Fc + (size_t)32 * LDp;         // 32 x 32 inverse diagonal block
   T *Tt = Lv + 1024;                     // 32 x MT backward temporaries
   __shared__ int s_task;
-  const int tid = threadIdx.x, cg = tid & 7, rg = tid >> 3;
+  const int tid = threadIdx.x, cg = tid % CG, rg = tid / CG;
   T *Xs = scratch + (long long)blockIdx.x * scratch_stride;
   for (;;) {
     if (tid == 0) s_task = atomicAdd(counter, 1);
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     const int s = task_s[task], j0 = task_j0[task];
     const DevTpl t = D.tpl[D.sub_tpl[s]];
     const int n = t.n, LD = t.LD, b = t.b, m = t.nbnd;
-    const int ncol = min(MRHS_T, m - j0);
+    const int ncol = min(MT, m - j0);
     const int *bnd = D.pool + t.bnd;
     const int *cptr = D.pool + t.csr_ptr, *ccol = D.pool + t.csr_col;
     const int *isb = D.pool + t.is_bnd;
@@ -61,16 +63,16 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     const T *Li = linv + linv_off[s];
     auto fixed = [&](int d) { return t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2); };
     // ---- right-hand sides into the scratch block (row r at Xs + r * MT) ----
-    for (long long i = tid; i < (long long)n * MRHS_T; i += blockDim.x) Xs[i] = T(0);
+    for (long long i = tid; i < (long long)n * MT; i += blockDim.x) Xs[i] = T(0);
     __syncthreads();
     for (int jj = tid; jj < ncol; jj += blockDim.x) {
       const int c = bnd[j0 + jj];
       if (kind == 0) {
-        if (!fixed(c)) Xs[(long long)c * MRHS_T + jj] = T(1);
+        if (!fixed(c)) Xs[(long long)c * MT + jj] = T(1);
       } else {
         for (int e = cptr[c]; e < cptr[c + 1]; ++e) {
           const int i = ccol[e];
-          if (!isb[i]) Xs[(long long)i * MRHS_T + jj] = T(-val[e]);
+          if (!isb[i]) Xs[(long long)i * MT + jj] = T(-val[e]);
         }
       }
     }
@@ -80,9 +82,9 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     int hi = 0;
     for (int k = 0; k < nb; ++k) {
       const int r0 = 32 * k, ncb = min(32, n - r0), rend = min(n, r0 + 32 + b);
-      for (int idx = tid; idx < (rend - hi) * MRHS_T; idx += blockDim.x) {
-        const int r = hi + idx / MRHS_T, q = idx % MRHS_T;
-        Wn[(r % R) * MRHS_T + q] = Xs[(long long)r * MRHS_T + q];
+      for (int idx = tid; idx < (rend - hi) * MT; idx += blockDim.x) {
+        const int r = hi + idx / MT, q = idx % MT;
+        Wn[(r % R) * MT + q] = Xs[(long long)r * MT + q];
       }
       hi = max(hi, rend);
       for (int idx = tid; idx < ncb * LD; idx += blockDim.x) {
@@ -93,18 +95,20 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       __syncthreads();
       // diagonal block: y_k = Linv_k w_k (rows past n are never loaded: c < ncb)
       T y[4] = {T(0), T(0), T(0), T(0)};
-      for (int c = 0; c < ncb; ++c) {
-        const T l = Lv[rg * 32 + c];
-        T w[4];
-        ld4(Wn + ((r0 + c) % R) * MRHS_T + 4 * cg, w);
+      if (rg < 32) {
+        for (int c = 0; c < ncb; ++c) {
+          const T l = Lv[rg * 32 + c];
+          T w[4];
+          ld4(Wn + ((r0 + c) % R) * MT + 4 * cg, w);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) y[q] += l * w[q];
+          for (int q = 0; q < 4; ++q) y[q] += l * w[q];
+        }
       }
       __syncthreads();
       if (rg < ncb) {
         const T dinv = Fc[rg * LDp + (r0 + rg) % LD];
-        T *wr = Wn + ((r0 + rg) % R) * MRHS_T + 4 * cg;
-        T *xr = Xs + (long long)(r0 + rg) * MRHS_T + 4 * cg;
+        T *wr = Wn + ((r0 + rg) % R) * MT + 4 * cg;
+        T *xr = Xs + (long long)(r0 + rg) * MT + 4 * cg;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           wr[q] = y[q];
@@ -120,11 +124,11 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
         for (int q = 0; q < 4; ++q) acc[i][q] = T(0);
       for (int c = 0; c < ncb; ++c) {
         T yc[4];
-        ld4(Wn + ((r0 + c) % R) * MRHS_T + 4 * cg, yc);
+        ld4(Wn + ((r0 + c) % R) * MT + 4 * cg, yc);
         const T *col = Fc + c * LDp;
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
-          const int r = r0 + 32 + rg + 32 * i;
+          const int r = r0 + 32 + rg + RG * i;
           const T l = (r < rend && r - (r0 + c) <= b) ? col[r % LD] : T(0);
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[i][q] += l * yc[q];
@@ -132,9 +136,9 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       }
 #pragma unroll
       for (int i = 0; i < NR; ++i) {
-        const int r = r0 + 32 + rg + 32 * i;
+        const int r = r0 + 32 + rg + RG * i;
         if (r < rend) {
-          T *wr = Wn + (r % R) * MRHS_T + 4 * cg;
+          T *wr = Wn + (r % R) * MT + 4 * cg;
 #pragma unroll
           for (int q = 0; q < 4; ++q) wr[q] -= acc[i][q];
         }
@@ -152,33 +156,37 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       __syncthreads();
       T tv[4] = {T(0), T(0), T(0), T(0)};
       if (rg < ncb) {
-        ld4(Xs + (long long)(r0 + rg) * MRHS_T + 4 * cg, tv);
+        ld4(Xs + (long long)(r0 + rg) * MT + 4 * cg, tv);
         const T *col = Fc + rg * LDp;
         const int j = r0 + rg;
         for (int r = r0 + 32; r < rtop; ++r) {
           const T l = (r - j <= b) ? col[r % LD] : T(0);
           T x4[4];
-          ld4(Wn + (r % R) * MRHS_T + 4 * cg, x4);
+          ld4(Wn + (r % R) * MT + 4 * cg, x4);
 #pragma unroll
           for (int q = 0; q < 4; ++q) tv[q] -= l * x4[q];
         }
       }
+      if (rg < 32) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Tt[rg * MRHS_T + 4 * cg + q] = tv[q];
+        for (int q = 0; q < 4; ++q) Tt[rg * MT + 4 * cg + q] = tv[q];
+      }
       __syncthreads();
       // within the block: x_k = Linv_k^T t
       T x[4] = {T(0), T(0), T(0), T(0)};
+      if (rg < 32) {
 #pragma unroll 8
-      for (int c = 0; c < 32; ++c) {
-        const T l = Lv[c * 32 + rg];
-        T tc[4];
-        ld4(Tt + c * MRHS_T + 4 * cg, tc);
+        for (int c = 0; c < 32; ++c) {
+          const T l = Lv[c * 32 + rg];
+          T tc[4];
+          ld4(Tt + c * MT + 4 * cg, tc);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] += l * tc[q];
+          for (int q = 0; q < 4; ++q) x[q] += l * tc[q];
+        }
       }
       if (rg < ncb) {
-        T *wr = Wn + ((r0 + rg) % R) * MRHS_T + 4 * cg;
-        T *xr = Xs + (long long)(r0 + rg) * MRHS_T + 4 * cg;
+        T *wr = Wn + ((r0 + rg) % R) * MT + 4 * cg;
+        T *xr = Xs + (long long)(r0 + rg) * MT + 4 * cg;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           wr[q] = x[q];
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     if (kind == 0) {
       for (int idx = tid; idx < m * ncol; idx += blockDim.x) {
         const int a = idx / ncol, jj = idx - a * ncol;
-        O[(long long)a * mp + j0 + jj] = Xs[(long long)bnd[a] * MRHS_T + jj];
+        O[(long long)a * mp + j0 + jj] = Xs[(long long)bnd[a] * MT + jj];
       }
     } else {
       // S[a][j] = sum_c K[b_a][c] (y_j[c] + [c == b_j]);  y_j vanishes on the rows of b
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
         double acc = 0.0;
         for (int e = cptr[row]; e < cptr[row + 1]; ++e) {
           const int c = ccol[e];
-          acc += val[e] * ((double)Xs[(long long)c * MRHS_T + jj] + (c == cj ? 1.0 : 0.0));
+          acc += val[e] * ((double)Xs[(long long)c * MT + jj] + (c == cj ? 1.0 : 0.0));
         }
         O[(long long)a * mp + j0 + jj] = T(acc);
       }
@@ -362,54 +370,71 @@ cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const floa
 }
 
 // ------------------------------------ launchers --------------------------------------
-template <typename T, int NR>
+template <typename T, int NR, int MT>
 static cudaError_t launch_mrhs_T(int grid, cudaStream_t st, const int *ts, const int *tj, int ntask, DevTopo D,
                                  const T *fac, const T *linv, const long long *loff, const double *csr, int kind,
                                  T *scratch, long long sstride, int *counter, T *out, const long long *ooff, int R,
                                  int LDp, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_band_mrhs<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_band_mrhs<T, NR, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_band_mrhs<T, NR><<<grid, 256, smem, st>>>(ts, tj, ntask, D, fac, linv, loff, csr, kind, scratch, sstride,
-                                              counter, out, ooff, R, LDp);
+  k_band_mrhs<T, NR, MT><<<grid, 256, smem, st>>>(ts, tj, ntask, D, fac, linv, loff, csr, kind, scratch, sstride,
+                                                  counter, out, ooff, R, LDp);
   return cudaGetLastError();
 }
 
-size_t mrhs_smem_bytes(bool fp32, int R, int LDp) {
+size_t mrhs_smem_bytes(bool fp32, int R, int LDp, int mt) {
   const size_t esz = fp32 ? 4 : 8;
-  return esz * ((size_t)R * MRHS_T + 32 * (size_t)LDp + 1024 + 32 * MRHS_T);
+  return esz * ((size_t)R * mt + 32 * (size_t)LDp + 1024 + 32 * (size_t)mt);
 }
 
-cudaError_t launch_band_mrhs(bool fp32, int nr, int grid, cudaStream_t st, const int *task_s, const int *task_j0,
-                             int ntask, DevTopo D, const void *fac, const void *linv, const long long *linv_off,
-                             const double *csr, int kind, void *scratch, long long sstride, int *counter, void *out,
-                             const long long *out_off, int R, int LDp) {
-  const size_t smem = mrhs_smem_bytes(fp32, R, LDp);
-#define FP_MRHS(TT, N)                                                                                        \
-  return launch_mrhs_T<TT, N>(grid, st, task_s, task_j0, ntask, D, (const TT *)fac, (const TT *)linv, linv_off, \
-                              csr, kind, (TT *)scratch, sstride, counter, (TT *)out, out_off, R, LDp, smem)
+// rows per thread of the forward coupling for half bandwidth b: ceil(b / RG), RG = 256 / (MT / 4)
+static int mrhs_nr(int b, int mt) {
+  const int rg = 256 / (mt / 4);
+  const int nr = (b + rg - 1) / rg;
+  return nr <= 4 ? 4 : nr <= 8 ? 8 : nr <= 12 ? 12 : nr <= 16 ? 16 : 0;
+}
+
+template <typename T, int MT>
+static const void *mrhs_fn(int nr) {
+  return nr == 4 ? (const void *)k_band_mrhs<T, 4, MT> : nr == 8 ? (const void *)k_band_mrhs<T, 8, MT>
+         : nr == 12 ? (const void *)k_band_mrhs<T, 12, MT> : (const void *)k_band_mrhs<T, 16, MT>;
+}
+
+cudaError_t launch_band_mrhs(bool fp32, int bmax, int mt, int grid, cudaStream_t st, const int *task_s,
+                             const int *task_j0, int ntask, DevTopo D, const void *fac, const void *linv,
+                             const long long *linv_off, const double *csr, int kind, void *scratch, long long sstride,
+                             int *counter, void *out, const long long *out_off, int R, int LDp) {
+  const size_t smem = mrhs_smem_bytes(fp32, R, LDp, mt);
+  const int nr = mrhs_nr(bmax, mt);
+  if (nr == 0 || (mt != 32 && mt != 16)) return cudaErrorInvalidValue;
+#define FP_MRHS(TT, N, M)                                                                                       \
+  return launch_mrhs_T<TT, N, M>(grid, st, task_s, task_j0, ntask, D, (const TT *)fac, (const TT *)linv, linv_off, \
+                                 csr, kind, (TT *)scratch, sstride, counter, (TT *)out, out_off, R, LDp, smem)
+#define FP_MRHS_NR(TT, M)              \
+  if (nr == 4) FP_MRHS(TT, 4, M);      \
+  if (nr == 8) FP_MRHS(TT, 8, M);      \
+  if (nr == 12) FP_MRHS(TT, 12, M);    \
+  FP_MRHS(TT, 16, M)
   if (fp32) {
-    if (nr <= 4) FP_MRHS(float, 4);
-    if (nr <= 8) FP_MRHS(float, 8);
-    if (nr <= 12) FP_MRHS(float, 12);
-    FP_MRHS(float, 16);
+    if (mt == 32) { FP_MRHS_NR(float, 32); }
+    FP_MRHS_NR(float, 16);
   }
-  if (nr <= 4) FP_MRHS(double, 4);
-  if (nr <= 8) FP_MRHS(double, 8);
-  if (nr <= 12) FP_MRHS(double, 12);
-  FP_MRHS(double, 16);
+  if (mt == 32) { FP_MRHS_NR(double, 32); }
+  FP_MRHS_NR(double, 16);
+#undef FP_MRHS_NR
 #undef FP_MRHS
 }
 
-// resident CTAs per SM of the build kernel at this shared-memory size
-int mrhs_blocks_per_sm(bool fp32, int nr, int R, int LDp) {
-  const size_t smem = mrhs_smem_bytes(fp32, R, LDp);
-  int nb = 0;
-  const void *f = nullptr;
-  if (fp32) f = nr <= 4 ? (const void *)k_band_mrhs<float, 4> : nr <= 8 ? (const void *)k_band_mrhs<float, 8>
-              : nr <= 12 ? (const void *)k_band_mrhs<float, 12> : (const void *)k_band_mrhs<float, 16>;
-  else f = nr <= 4 ? (const void *)k_band_mrhs<double, 4> : nr <= 8 ? (const void *)k_band_mrhs<double, 8>
-           : nr <= 12 ? (const void *)k_band_mrhs<double, 12> : (const void *)k_band_mrhs<double, 16>;
+// resident CTAs per SM of the build kernel at this shared-memory size (0: does not fit)
+int mrhs_blocks_per_sm(bool fp32, int bmax, int mt, int R, int LDp) {
+  const size_t smem = mrhs_smem_bytes(fp32, R, LDp, mt);
+  const int nr = mrhs_nr(bmax, mt);
+  if (nr == 0 || smem > 227 * 1024) return 0;
+  const void *f = fp32 ? (mt == 32 ? mrhs_fn<float, 32>(nr) : mrhs_fn<float, 16>(nr))
+                       : (mt == 32 ? mrhs_fn<double, 32>(nr) : mrhs_fn<double, 16>(nr));
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, 256, smem) != cudaSuccess) return 0;
   return nb;
 }

@@ -216,7 +216,8 @@ __global__ void k_halo(DevTopo D, const double *csr_val, const double *xb, doubl
 }
 
 // z_b = K_{b .} (y + xb) on the rows of b (the Schur complement S_s xb, since y solves the
-// Dirichlet problem); written back into xb at the rows of b.
+// Dirichlet problem); written back into xb at the rows of b.  y = null: z_b = K_bb xb (xb is
+// zero off the rows of b), the lumped preconditioner's local operator.
 __global__ void k_bnd_apply(DevTopo D, const double *csr_val, const double *y, double *xb, const int *fl) {
   if (fl && fl[FL_DONE]) return;
   extern __shared__ double zsh[];
@@ -232,7 +233,7 @@ __global__ void k_bnd_apply(DevTopo D, const double *csr_val, const double *y, d
     double acc = 0.0;
     for (int e = cptr[row]; e < cptr[row + 1]; ++e) {
       const int c = ccol[e];
-      acc += val[e] * (ys[c] + xs[c]);
+      acc += val[e] * ((ys ? ys[c] : 0.0) + xs[c]);
     }
     zsh[q] = acc;
   }

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "FP_OK", 1: "FP_ERR_INVALID", 2: "FP_ERR_OOM", 3: "FP_ERR_CUD
 globals().update({name: code for code, name in STATUS_NAMES.items()})
 FP_SOURCE_MANUFACTURED, FP_SOURCE_POINT, FP_SOURCE_MANUFACTURED_T = 0, 1, 2
 FP_PREC_FP64, FP_PREC_MIXED = 0, 1
-FP_PRECOND_DIRICHLET, FP_PRECOND_NONE = 0, 2
+FP_PRECOND_DIRICHLET, FP_PRECOND_LUMPED, FP_PRECOND_NONE, FP_PRECOND_AUTO = 0, 1, 2, 3
 
 EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_get_sizes",
             "fp_get_lambda", "fp_get_lambda_keys", "fp_get_fields", "fp_get_subdomain", "fp_set_initial",
@@ -71,7 +71,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("factor_nb", ctypes.c_int), ("solve_wpc", ctypes.c_int), ("solve_chunk", ctypes.c_int),
                 ("solve_ctas_per_sm", ctypes.c_int), ("factor_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("explicit_ms", ctypes.c_double)]
+                ("explicit_ms", ctypes.c_double), ("precond", ctypes.c_int),
+                ("precond_rate", ctypes.c_double * 2), ("precond_ms_per_it", ctypes.c_double * 2)]
 
 
 class StepStats(ctypes.Structure):
@@ -157,7 +158,8 @@ class Solver:
         par = Params(case.lame_lambda, case.mu, case.alpha, case.c0, case.perm_k, case.mu_f, case.tau,
                      perm_ptr, src, int(case.src_node[0]), int(case.src_node[1]), float(case.q_omega),
                      FP_PREC_MIXED if prec == "mixed" else FP_PREC_FP64,
-                     FP_PRECOND_NONE if case.precond == "none" else FP_PRECOND_DIRICHLET,
+                     {"dirichlet": FP_PRECOND_DIRICHLET, "lumped": FP_PRECOND_LUMPED, "none": FP_PRECOND_NONE,
+                      "auto": FP_PRECOND_AUTO}[case.precond],
                      case.tol, case.max_it)
         st = _lib.fp_create(ctypes.byref(mesh), ctypes.byref(par), stream, ctypes.byref(self._h))
         if st != FP_OK:
@@ -341,7 +343,10 @@ class Solver:
     def tuning(self):
         t = Tuning()
         self._check(_lib.fp_get_tuning(self._h, ctypes.byref(t)))
-        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+        out = {k: getattr(t, k) for k, _ in Tuning._fields_}
+        for k in ("precond_rate", "precond_ms_per_it"):
+            out[k] = list(out[k])
+        return out
 
     def kernel_stats(self, kind):
         s = KernelStats()

@@ -81,7 +81,7 @@ class Case:
     tol: float = 1e-10
     max_it: int = 1000
     precision: str = "fp64"              # "fp64" | "mixed"
-    precond: str = "dirichlet"           # "dirichlet" | "lumped" | "none"
+    precond: str = "dirichlet"           # "dirichlet" | "lumped" | "none" | "auto"
     extra: dict = field(default_factory=dict)
 
     @property

@@ -103,3 +103,51 @@ def test_krylov_against_dense():
     x, k, h = minres(lambda v: A_ind @ v, lambda v: Mi @ v, b, np.zeros(n), 1e-12, np.linalg.norm(b), 500)
     assert _rel(x, np.linalg.solve(A_ind, b)) < 1e-9
     assert abs(h[-1] - np.linalg.norm(b - A_ind @ x)) < 1e-10 * np.linalg.norm(b)
+
+
+def _three_field_dense(case, L):
+    """Dense 3-field local matrix (eta eliminated) in the order [free u, xi, free p], built
+    from the full element-level matrices alone (not from the oracle's 4-field system)."""
+    A = L.A_full[L.ufree][:, L.ufree].toarray()
+    B = L.B_full[:, L.ufree].toarray()
+    R = L.R_full.toarray()
+    lam, al, c0 = case.lame_lambda, case.alpha, case.c0
+    if not L.m.is_poro:
+        return np.block([[A, B.T], [B, -R / lam]])
+    pf = L.pfree
+    Af = L.Af_full.toarray()[np.ix_(pf, pf)]
+    Rxp = (al / lam) * R[:, pf]
+    Rpp = R[np.ix_(pf, pf)]
+    Z = np.zeros((A.shape[0], pf.size))
+    return np.block([[A, B.T, Z], [B, -R / lam, Rxp], [Z.T, Rxp.T, -(c0 + al * al / lam) * Rpp - case.tau * Af]])
+
+
+def test_preconditioner_blocks_against_dense_three_field():
+    """The lumped local operator is the interface block of the 3-field matrix, and the
+    Dirichlet Schur complement of the oracle's 4-field system equals the 3-field one (eta is
+    interior): both against a dense assembly from the element-level matrices."""
+    case = W.small_case(3, 4, 2, k=2, lame_lambda=9.0, alpha=0.7, c0=0.4, tau=0.05)
+    fe = FETI(case, precond="lumped")
+    for s, L in enumerate(fe.Ls):
+        bd = fe.bd[s]
+        if bd.size == 0:
+            continue
+        K3 = _three_field_dense(case, L)
+        nP = L.m.n_pnode
+        b3 = np.where(bd < L.nu, bd, bd - (L.off_p - L.nu - nP)) if L.m.is_poro else bd
+        i3 = np.setdiff1d(np.arange(K3.shape[0]), b3)
+        Kbb = K3[np.ix_(b3, b3)]
+        assert np.abs(fe.Kbb3[s] - Kbb).max() <= 1e-13 * np.abs(Kbb).max(), s
+        S3 = Kbb - K3[np.ix_(b3, i3)] @ np.linalg.solve(K3[np.ix_(i3, i3)], K3[np.ix_(i3, b3)])
+        S4 = np.stack([fe.S_apply(s, e) for e in np.eye(bd.size)], axis=1)
+        assert np.abs(S4 - S3).max() <= 1e-9 * np.abs(S3).max(), s
+
+
+@pytest.mark.parametrize("precond", ["lumped", "none"])
+def test_feti_other_preconditioners_equal_monolithic(precond):
+    case = W.small_case(4, 4, 3, k=2, lame_lambda=49.0, tau=1e-3, n_steps=2, tol=1e-12, max_it=3000)
+    d = Discretization(case)
+    mono = solve_monolithic(case, d)
+    fe = FETI(case, d, precond=precond).run()
+    for a, b in zip(mono, fe):
+        assert _rel(b["lambda"], a["lambda"]) < 1e-8
