@@ -365,13 +365,95 @@ def run_native(args):
     return 0
 
 
+def run_config4(args):
+    """Learned lambda_0 on its own workload (config 4: config-3 geometry, point source): the
+    network is trained on the steps the solver records at the training source location
+    (seed 0, 400 steps), then 200 steps at an unseen location (seed 1) are run twice, with
+    the previous-step guess and with the learned guess; iterations and device time per step
+    at the metric's tolerance are compared.  Training is setup, outside the timed runs."""
+    import numpy as np
+    import torch
+    from paper_2509_06673_gb300 import build
+    build.build()
+    from paper_2509_06673_gb300 import fetipe as F
+    from paper_2509_06673_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    n_train, n_eval = args.config4_train, args.config4_eval
+
+    def solver(seed):
+        c = W.config4(seed=seed).with_(tol=1e-8, max_it=2000)
+        if args.precond:
+            c = c.with_(precond=args.precond)
+        sol = F.Solver(c, stream=stream.cuda_stream)
+        sol.set_option("explicit", args.explicit)
+        sol.assemble()
+        sol.factor()
+        return sol
+
+    t0 = time.perf_counter()
+    tr = solver(0)
+    tr.learned_record(True, max_samples=4_000_000)
+    for _ in range(n_train):
+        tr.step()
+    record_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = tr.learned_train(epochs=args.learned_epochs, batch=4096, lr=2e-3, seed=1)
+    train_s = time.perf_counter() - t0
+    theta = tr.mlp_get_params()
+    tr.close()
+
+    def evaluate(learned):
+        sol = solver(1)
+        if learned:
+            sol.mlp_set_params(theta)
+            sol.learned_use(True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, wins, gres = [], 0, []
+        for _ in range(n_eval):
+            st = sol.step()
+            its.append(st["iterations"])
+            wins += st["lambda0_learned"]
+            if learned and st["guess_res_prev"] > 0:
+                gres.append(st["guess_res_learned"] / st["guess_res_prev"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        lam = sol.get_lambda()
+        sol.close()
+        return its, wins, ms, lam, gres
+
+    its0, _, ms0, lam0, _ = evaluate(False)
+    its1, wins, ms1, lam1, gres = evaluate(True)
+    line = {"metric": METRIC, "value": n_eval / (ms1 / 1000.0), "unit": "steps/s", "n_gpus": 1,
+            "steps": n_eval, "warmup": 0, "ms_per_step": ms1 / n_eval, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 local / f64 outer", "data": "synthetic",
+            "config": {"workload": "config4: config-3 geometry (32x32 subdomains, uneven 16..48 cells, P2, "
+                                   "nu=0.49), point source; train seed 0, evaluate seed 1",
+                       "train_steps": n_train, "eval_steps": n_eval, "tol": 1e-8,
+                       "explicit_operators": bool(args.explicit), "record_s": record_s, "train_s": train_s,
+                       "train_loss": loss},
+            "learned_gain": {"its_prev_guess": int(np.sum(its0)), "its_learned": int(np.sum(its1)),
+                             "iteration_ratio": float(np.sum(its1) / np.sum(its0)),
+                             "steps_per_s_prev_guess": n_eval / (ms0 / 1000.0),
+                             "steps_per_s_learned": n_eval / (ms1 / 1000.0),
+                             "time_ratio": ms1 / ms0, "learned_guess_chosen": int(wins),
+                             "median_start_residual_ratio": float(np.median(gres)) if gres else None,
+                             "lambda_rel_diff": float(np.abs(lam1 - lam0).max() / np.abs(lam0).max())}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--config", default="config5", choices=["config2", "config3", "config5", "config5s"])
+    ap.add_argument("--config", default="config5", choices=["config2", "config3", "config4", "config5", "config5s"])
+    ap.add_argument("--config4-train", type=int, default=400, help="config4: recorded training steps")
+    ap.add_argument("--config4-eval", type=int, default=200, help="config4: evaluation steps")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
@@ -393,6 +475,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "config4":
+        return run_config4(args)
     return run_native(args)
 
 

@@ -117,9 +117,12 @@ typedef struct {
   int iterations;            /* PCG iterations */
   double rel_residual;       /* recursive ||P r|| / ||P(d - F lambda_00)|| at exit */
   double true_rel_residual;  /* the same with r recomputed from lambda at exit */
-  int lambda0_learned;       /* 1 if the learned initial guess won the judge this step */
+  int lambda0_learned;       /* 1 if the learned guess moved lambda_0 off the lambda^{n-1} guess:
+                                the judge minimises the true residual over the span of lambda^{n-1},
+                                the extrapolation and the network's correction (see
+                                fp_learned_use) */
   double guess_res_prev;     /* relative true residual of the lambda^{n-1} guess (-1: not computed) */
-  double guess_res_learned;  /* relative true residual of the learned guess (-1: not computed) */
+  double guess_res_learned;  /* relative true residual of the learned lambda_0 (-1: not computed) */
   int restarts;              /* restarts of Algorithm 1 from the true residual */
   int stagnations;           /* rounds stopped because the recursive residual stalled */
 } fp_step_stats;
@@ -234,19 +237,22 @@ fp_status fp_get_dof_map(const fp_handle *h, int s, int *field, int *node, int *
 fp_status fp_get_local_matrix(const fp_handle *h, int s, double *dense);
 
 /* Device time of the last fp_step split by phase (milliseconds, CUDA events):
- * [0] rhs + d, [1] PCG loop, [2] recovery; [3] total local-solve time of the step. */
+ * [0] right-hand side, d and the initial guess, [1] the PCG loop with its restarts,
+ * [2] recovery and history; [3] the number of restarts of the step. */
 fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
 
 /* ---------------- learned initial guess (not in the paper: a library pattern) ----------
  * A 3-layer MLP (8 -> 256 -> 256 -> 1, ReLU; the 256 x 256 products on tensor cores with
  * bfloat16 operands and FP32 accumulation) maps per-multiplier features (the last increment
- * lambda^{n-1} - lambda^{n-2} and lambda^{n-1}, each divided by its RMS; the ratio rho of the
- * last two increments of the source's time signal; rho times the first feature; the node
- * position; kind and component) to a correction of the source-scaled extrapolation: the
- * predicted increment, in units of the RMS of the last one, is rho * (last increment) + MLP.
- * With fp_learned_use on, fp_step computes both guesses lambda_00 + P lambda^{n-1} and
- * lambda_00 + P(lambda^{n-1} + s (x3 + MLP)) and keeps the one with the smaller true projected
- * residual (the judge); lambda^{n-1} is the fallback.  Parameters: one flat FP32 array of
+ * dl = lambda^{n-1} - lambda^{n-2} and lambda^{n-1}, each divided by its RMS; the ratio rho of
+ * the last two increments of the source's time signal; three products of these; kind and
+ * component; every input clamped to [-8, 8]) to a correction of the source-scaled
+ * extrapolation, in units of s = RMS(dl).  With fp_learned_use on, fp_step forms the
+ * directions tc = P(rho dl) and tb = P(s MLP) from lambda_a = lambda_00 + P lambda^{n-1} and
+ * takes lambda_0 = lambda_a + a tc + b tb with (a, b) minimising the true projected residual
+ * ||P(d - F lambda_0)||_2 (the judge: a 2 x 2 least-squares problem, two more accurate F
+ * applications); (a, b) = (0, 0), the previous-step guess, is the fallback and never beaten
+ * by the result.  Parameters: one flat FP32 array of
  * 68353 values: W1 [8 x 256] row-major, b1 [256], W2 [256 x 256] row-major, b2 [256],
  * W3 [256], b3 [1]. */
 fp_status fp_learned_record(fp_handle *h, int on, long long max_samples, int per_step);
@@ -316,10 +322,7 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *   "stag_window"  [60] a round of Algorithm 1 stops (and restarts from the true residual)
  *                       when its recursive residual has not halved within this many
  *                       iterations; 0 never, 1..100000
- *   "judge"        [0]  how the learned lambda_0 is judged against the previous-step guess:
- *                       0 the 2-norm of the projected residual P r, 1 the preconditioned
- *                       residual (P r, P M^-1 P r), an estimate of the error in the F-norm
- *                       (two more preconditioner applications per step) */
+ */
 fp_status fp_set_option(fp_handle *h, const char *key, double value);
 
 /* Per-kernel-class timing (CUDA events on the handle's stream around every launch of the

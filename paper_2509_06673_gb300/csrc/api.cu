@@ -90,12 +90,14 @@ __global__ void k_adam(float *, const float *, float *, float *, int, float, flo
 __global__ void k_mlp_init(float *, unsigned long long);
 __global__ void k_features(int, const double *, const double *, const double *, const double *, const float *,
                            const int *, const int *, float *, float *);
-__global__ void k_guess(int, const double *, const float *, const float *, const double *, double *);
-__global__ void k_record(int, const float *, const double *, const double *, const double *, int, int, long long,
-                         long long, float *, float *);
+__global__ void k_guess_dirs(int, const double *, const double *, const float *, const double *, const double *,
+                             double *, double *);
+__global__ void k_span_solve(const double *, double *, int *);
+__global__ void k_span_apply(int, double *, double *, const double *, const double *, const double *,
+                             const double *, const double *);
+__global__ void k_record(int, const float *, const double *, const double *, const double *, const double *,
+                         const double *, int, int, long long, long long, float *, float *);
 __global__ void k_gather_rows(int, const int *, const float *, const float *, float *, float *);
-__global__ void k_choose(int, double *, double *, const double *, const double *, const double *, const double *,
-                         int *);
 
 }  // namespace fp
 
@@ -158,7 +160,6 @@ struct fp_handle {
   int pcg_chunk = 8;       // PCG iterations per body of the device loop (per host poll without graphs)
   int use_graph = 1;       // 1: each time step is one CUDA graph launch (device-side loops)
   int stag_window = 60;    // PCG round stops after this many iterations without halving
-  int judge = 0;           // learned guess judged by 0: ||P r||_2, 1: (P r, P M^-1 P r)
   int restarts_last = 0;
   // per-step graph: captured on private streams, launched on `stream`
   cudaStream_t cap[3] = {};
@@ -202,6 +203,8 @@ struct fp_handle {
   int *kind_rows = nullptr, *comp_rows = nullptr, *idx_dev = nullptr, *choose_flag = nullptr;
   double *lam_prev2 = nullptr, *lam_b = nullptr, *r_b = nullptr;
   float *SX = nullptr, *SY = nullptr;
+  int *train_idx = nullptr;  // shuffled sample indices of fp_learned_train (grown on demand)
+  long long train_idx_cap = 0;
   long long n_samples = 0, cap_samples = 0;
   int mlp_ready = 0, learned_use = 0, learned_record = 0, adam_step = 0, hist = 0;
   int record_per_step = 65536;
@@ -439,7 +442,7 @@ fp_status build_device(fp_handle *h) {
     TRY(dalloc(h, &h->xb, (size_t)CH * MLP_NIN));
     TRY(dalloc(h, &h->fscale, 1));
     TRY(dalloc(h, &h->loss_rows, CH)); TRY(dalloc(h, &h->loss_acc, 1));
-    TRY(dalloc(h, &h->fsum, 2)); TRY(dalloc(h, &h->nrm, 4));
+    TRY(dalloc(h, &h->fsum, 2)); TRY(dalloc(h, &h->nrm, 10));
     TRY(dalloc(h, &h->idx_dev, CH)); TRY(dalloc(h, &h->choose_flag, 1));
     for (double **v : {&h->lam_prev2, &h->lam_b, &h->r_b}) TRY(dalloc(h, v, (size_t)nl));
     CK(cudaMemsetAsync(h->lam_prev2, 0, nl * sizeof(double), h->stream));
@@ -1186,35 +1189,34 @@ fp_status step_prologue(fp_handle *h, bool use_learned) {
   TRY(apply_F(h, h->lam, h->q, h->fl_zero));
   TRY(lincomb(h, h->r, h->d, 1.0, h->q, -1.0, nullptr));
   TRY(apply_P(h, h->r, h->r, h->fl_zero));
-  // learned lambda_0: the MLP predicts the next increment; the judge keeps whichever guess
-  // has the smaller true projected residual (lambda^{n-1} is the fallback)
+  // learned lambda_0: the network predicts a correction to the source-scaled extrapolation;
+  // the judge takes the point of smallest true projected residual on the affine span of
+  // lambda_a = lambda_00 + P lambda^{n-1} (the fallback), the extrapolation and the network's
+  // correction (two more accurate F applications).  nrm: [0] ||r_a||^2, [1] ||r_0||^2,
+  // [2..6] the Gram entries, [7..8] the coefficients.
   if (use_learned) {
+    double *tc = h->t2, *tb = h->lam_b, *u = h->q, *w = h->r_b;
     TRY(build_features(h));
     TRY(mlp_forward(h, h->Xf, nl, h->mout));
-    k_guess<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam_prev, h->mout, h->Xf, h->fsum, h->t2);
+    k_guess_dirs<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam_prev, h->lam_prev2, h->mout, h->stepv, h->fsum, tc,
+                                                   tb);
     CKL();
-    TRY(apply_P(h, h->t2, h->t2, h->fl_zero));
-    TRY(lincomb(h, h->lam_b, h->lam00, 1.0, h->t2, 1.0, nullptr));
-    TRY(apply_F(h, h->lam_b, h->q, h->fl_zero));
-    TRY(lincomb(h, h->r_b, h->d, 1.0, h->q, -1.0, nullptr));
-    TRY(apply_P(h, h->r_b, h->r_b, h->fl_zero));
+    TRY(apply_P(h, tc, tc, h->fl_zero));
+    TRY(apply_P(h, tb, tb, h->fl_zero));
+    TRY(apply_F(h, tc, u, h->fl_zero));
+    TRY(apply_P(h, u, u, h->fl_zero));
+    TRY(apply_F(h, tb, w, h->fl_zero));
+    TRY(apply_P(h, w, w, h->fl_zero));
     TRY(dot(h, h->r, h->r, OP_STORE, h->nrm, nullptr));
-    TRY(dot(h, h->r_b, h->r_b, OP_STORE, h->nrm + 1, nullptr));
-    const double *na = h->nrm, *nb = h->nrm + 1;
-    if (h->judge == 1) {
-      // preconditioned residual norms: (P r, P M^-1 P r) approximates the F-norm of the error,
-      // the quantity the convergence bound of Algorithm 1 starts from
-      TRY(apply_M(h, h->r, h->t1, h->fl_zero));
-      TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
-      TRY(dot(h, h->r, h->t1, OP_STORE, h->nrm + 2, nullptr));
-      TRY(apply_M(h, h->r_b, h->t1, h->fl_zero));
-      TRY(apply_P(h, h->t1, h->t1, h->fl_zero));
-      TRY(dot(h, h->r_b, h->t1, OP_STORE, h->nrm + 3, nullptr));
-      na = h->nrm + 2;
-      nb = h->nrm + 3;
-    }
-    k_choose<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam, h->r, h->lam_b, h->r_b, na, nb, h->choose_flag);
+    TRY(dot(h, u, u, OP_STORE, h->nrm + 2, nullptr));
+    TRY(dot(h, u, w, OP_STORE, h->nrm + 3, nullptr));
+    TRY(dot(h, w, w, OP_STORE, h->nrm + 4, nullptr));
+    TRY(dot(h, u, h->r, OP_STORE, h->nrm + 5, nullptr));
+    TRY(dot(h, w, h->r, OP_STORE, h->nrm + 6, nullptr));
+    k_span_solve<<<1, 1, 0, s>>>(h->nrm + 2, h->nrm + 7, h->choose_flag);
+    k_span_apply<<<(nl + 255) / 256, 256, 0, s>>>(nl, h->lam, h->r, tc, tb, u, w, h->nrm + 7);
     CKL();
+    TRY(dot(h, h->r, h->r, OP_STORE, h->nrm + 1, nullptr));
   }
   return FP_OK;
 }
@@ -1608,8 +1610,9 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
     const int stride = std::max(1, nl / per);
     const int r0 = (int)(h->step_n % stride);
     const long long cnt = (nl - r0 + stride - 1) / stride;
-    k_record<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(nl, h->Xf, h->lam, h->lam_prev, h->fsum, r0, stride,
-                                                           h->n_samples, h->cap_samples, h->SX, h->SY);
+    k_record<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(nl, h->Xf, h->lam, h->lam_prev, h->lam_prev2, h->stepv,
+                                                           h->fsum, r0, stride, h->n_samples, h->cap_samples, h->SX,
+                                                           h->SY);
     CKL();
     h->n_samples = std::min(h->cap_samples, h->n_samples + cnt);
   }
@@ -1979,8 +1982,14 @@ fp_status fp_learned_train(fp_handle *h, int epochs, int batch, double lr, unsig
   const long long ns = h->n_samples;
   const long long nb = ns / batch;
   std::vector<int> perm(ns);
-  int *didx = nullptr;
-  TRY(dalloc(h, &didx, (size_t)ns));
+  if (h->train_idx_cap < ns) {
+    if (h->train_idx) cudaFree(h->train_idx);
+    h->train_idx = nullptr;
+    h->train_idx_cap = 0;
+    CK(cudaMalloc(&h->train_idx, (size_t)ns * sizeof(int)));
+    h->train_idx_cap = ns;
+  }
+  int *didx = h->train_idx;
   double epoch_loss = 0;
   for (int e = 0; e < epochs; ++e) {
     for (long long i = 0; i < ns; ++i) perm[i] = (int)i;
@@ -2028,7 +2037,6 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "factor_fp64") { if (v < 0 || v > 1) return bad(); h->factor_fp64 = v; }
   else if (k == "graph") { if (v < 0 || v > 1) return bad(); h->use_graph = v; }
   else if (k == "stag_window") { if (v < 0 || v > 100000) return bad(); h->stag_window = v; }
-  else if (k == "judge") { if (v < 0 || v > 1) return bad(); h->judge = v; }
   else if (k == "solve_chunk") { if (v != 0 && (v < 4096 || v > 65536 || v % 1024)) return bad(); h->solve_chunk = v; }
   else if (k == "solve_cps") { if (v < 0 || v > 2) return bad(); h->solve_cps = v; }
   else if (k == "factor_nb") { if (v != 0 && (v < 4 || v > 64 || v % 4)) return bad(); h->factor_nb = v; }
@@ -2071,6 +2079,7 @@ const char *fp_last_error(const fp_handle *h) { return h ? h->err.c_str() : g_cr
 
 void fp_destroy(fp_handle *h) {
   if (!h) return;
+  if (h->train_idx) cudaFree(h->train_idx);
   drop_graph(h);
   for (auto &c : h->cap)
     if (c) cudaStreamDestroy(c);

@@ -234,7 +234,12 @@ __global__ void k_mlp_init(float *P, unsigned long long seed) {
 // Per multiplier r: [dl/s1, l1/s0, rho, rho*dl/s1, (dl/s1)(l1/s0), rho*l1/s0, kind, comp],
 // dl = l1 - l2 (features are free of the node position, so nothing ties the network to the
 // source location it was trained on),
-// s1 = RMS(dl), s0 = RMS(l1) (from the sums of squares in sums[0], sums[1]).
+// s1 = RMS(dl), s0 = RMS(l1) (from the sums of squares in sums[0], sums[1]).  The network
+// inputs are clamped to [-FEAT_CLAMP, FEAT_CLAMP]: a localised source (a point load) makes
+// the few rows near it hundreds of RMS units large, and such inputs made training diverge;
+// the extrapolation itself (the skip connection) is computed from lambda directly.
+constexpr float FEAT_CLAMP = 8.0f;
+__device__ __forceinline__ float clampf(double v) { return (float)fmin(fmax(v, -FEAT_CLAMP), FEAT_CLAMP); }
 __global__ void k_features(int n, const double *l1, const double *l2, const double *sums, const double *stepv,
                            const float *xy, const int *kind, const int *comp, float *X, float *scale_out) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -244,29 +249,33 @@ __global__ void k_features(int n, const double *l1, const double *l2, const doub
   if (r >= n) return;
   const double dl = (l1[r] - l2[r]) / s1;
   float *f = X + (long long)r * MLP_NIN;
-  f[0] = (float)dl;
-  f[1] = (float)(l1[r] / s0);
-  f[2] = (float)rho;
-  f[3] = (float)(rho * dl);
-  f[4] = (float)(dl * (l1[r] / s0));
-  f[5] = (float)(rho * (l1[r] / s0));
+  f[0] = clampf(dl);
+  f[1] = clampf(l1[r] / s0);
+  f[2] = clampf(rho);
+  f[3] = clampf(rho * dl);
+  f[4] = clampf(dl * (l1[r] / s0));
+  f[5] = clampf(rho * (l1[r] / s0));
   f[6] = (float)kind[r];
   f[7] = (float)comp[r];
 }
 
-// guess = l1 + s1 * (x3 + out): the network corrects the source-scaled extrapolation
-// x3 = rho (l1 - l2) / s1 (a skip connection; s1 recomputed from the same sums)
-__global__ void k_guess(int n, const double *l1, const float *out, const float *X, const double *sums, double *guess) {
+// The two directions of the learned guess from lambda^{n-1}: the source-scaled
+// extrapolation dc = rho (l1 - l2) (the network's skip connection, in FP64 from lambda
+// itself) and the network's correction db = s1 * out (s1 from the same sums).
+__global__ void k_guess_dirs(int n, const double *l1, const double *l2, const float *out, const double *stepv,
+                             const double *sums, double *dc, double *db) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const double s1 = sqrt(sums[0] / n);
-  guess[r] = l1[r] + s1 * ((double)X[(long long)r * MLP_NIN + 3] + (double)out[r]);
+  dc[r] = stepv[ST_RHO] * (l1[r] - l2[r]);
+  db[r] = s1 * (double)out[r];
 }
 
-// append samples (features, target = (l_new - l1)/s1 - x3: what the skip connection misses)
-// for rows r0, r0+stride, ...
-__global__ void k_record(int n, const float *X, const double *lnew, const double *l1, const double *sums, int r0,
-                         int stride, long long base, long long cap, float *SX, float *SY) {
+// append samples (features, target = (l_new - l1 - rho (l1 - l2)) / s1: what the skip
+// connection misses) for rows r0, r0+stride, ...
+__global__ void k_record(int n, const float *X, const double *lnew, const double *l1, const double *l2,
+                         const double *stepv, const double *sums, int r0, int stride, long long base, long long cap,
+                         float *SX, float *SY) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long r = r0 + q * stride;
   if (r >= n) return;
@@ -274,7 +283,7 @@ __global__ void k_record(int n, const float *X, const double *lnew, const double
   if (d >= cap) return;
   const double s1 = sqrt(sums[0] / n) + 1e-300;
   for (int k = 0; k < MLP_NIN; ++k) SX[d * MLP_NIN + k] = X[r * MLP_NIN + k];
-  SY[d] = (float)((lnew[r] - l1[r]) / s1 - (double)X[r * MLP_NIN + 3]);
+  SY[d] = (float)((lnew[r] - l1[r] - stepv[ST_RHO] * (l1[r] - l2[r])) / s1);
 }
 
 __global__ void k_gather_rows(int m, const int *idx, const float *SX, const float *SY, float *X, float *Y) {
@@ -286,16 +295,35 @@ __global__ void k_gather_rows(int m, const int *idx, const float *SX, const floa
   else Y[i] = SY[s];
 }
 
-// judge: keep the candidate with the smaller true projected residual.
-// a: (lam_a, r_a, nrm2 a), b: (lam_b, r_b, nrm2 b); writes into lam_a, r_a; flag = 1 if b won.
-__global__ void k_choose(int n, double *lam_a, double *r_a, const double *lam_b, const double *r_b,
-                         const double *na, const double *nb, int *flag) {
-  const bool use_b = *nb < *na;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r == 0) *flag = use_b ? 1 : 0;
-  if (r >= n || !use_b) return;
-  lam_a[r] = lam_b[r];
-  r_a[r] = r_b[r];
+// The judge: lambda_0 = lambda_a + a tc + b tb with (a, b) minimising the true projected
+// residual ||r_a - a u - b w||_2 (u = P F tc, w = P F tb; the residual is affine in lambda),
+// from g = (u.u, u.w, w.w, u.r_a, w.r_a); (0, 0), the previous-step guess, is one of the
+// candidates, so the result is never worse.  One thread.
+__global__ void k_span_solve(const double *g, double *ab, int *flag) {
+  const double uu = g[0], uw = g[1], ww = g[2], ur = g[3], wr = g[4];
+  double a = 0.0, b = 0.0;
+  const double det = uu * ww - uw * uw;
+  if (uu > 0.0 && ww > 0.0 && det > 1e-10 * uu * ww) {
+    a = (ur * ww - wr * uw) / det;
+    b = (uu * wr - uw * ur) / det;
+  } else if (uu > 0.0) {
+    a = ur / uu;
+  } else if (ww > 0.0) {
+    b = wr / ww;
+  }
+  if (!isfinite(a) || !isfinite(b)) a = b = 0.0;
+  ab[0] = a;
+  ab[1] = b;
+  *flag = (a != 0.0 || b != 0.0) ? 1 : 0;
+}
+
+__global__ void k_span_apply(int n, double *lam, double *r, const double *tc, const double *tb, const double *u,
+                             const double *w, const double *ab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = ab[0], b = ab[1];
+  lam[i] += a * tc[i] + b * tb[i];
+  r[i] -= a * u[i] + b * w[i];
 }
 
 // ------------------------------------ launchers --------------------------------------
