@@ -198,8 +198,9 @@ fp_status fp_get_subdomain(const fp_handle *h, int s, double *u, double *xi, dou
                            int on_device);
 
 /* Checkpoint / restore of the time-stepping state: step counter, lambda^n, lambda^{n-1},
- * R eta^n, the last fields, the source-signal history and the learned-guess network (its
- * parameters, Adam moments and step, and whether it is in use).  Not stored: matrices and
+ * R eta^n, the last fields, the source-signal history, the learned-guess network (its
+ * parameters, Adam moments and step, and whether it is in use) and the refinement's
+ * measured contraction.  Not stored: matrices and
  * factors (fp_assemble / fp_factor rebuild them bit for bit), options, recorded training
  * samples.  fp_restore needs a handle of the same problem after fp_assemble (FP_ERR_STATE
  * before; FP_ERR_INVALID for a file of another problem, a bad or truncated file); the
@@ -274,7 +275,10 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  * out of range.
  *   "ir_sweeps"    [6]  maximum FP64 refinement sweeps of the accurate local solves (mixed
  *                       precision: d = B K^+ f, the true residual, the recovery), 0..16
- *   "ir_eps"       [1e-12] refinement stops once ||dx||_2 <= ir_eps ||x||_2 (all subdomains)
+ *   "ir_eps"       [0]  refinement stops once ||dx||_2 <= ir_eps ||x||_2 (all subdomains) or
+ *                       once the predicted next correction (the last one times the last
+ *                       contraction measured on these factors) is below that; 0: 1e-2 tol,
+ *                       clamped to [1e-15, 1e-10]
  *   "ir_stag"      [0.5] ... or once ||dx||_2 > ir_stag ||dx_prev||_2 (stagnation at the
  *                       rounding floor), 0 <= ir_stag < 1, 0 never
  *   "inner_ir"     [0]  refinement sweeps of the local solves inside the PCG loop, 0..8

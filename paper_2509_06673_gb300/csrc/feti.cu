@@ -287,9 +287,12 @@ __global__ void k_residual_N(DevTopo D, const double *__restrict__ sell_val, con
 // eps ||x|| (a converging sweep multiplies the error by the FP32 solve's relative accuracy,
 // so x is then already that accurate); or, with stag2 > 0, once the correction stagnates
 // (||r||^2 > stag2 ||r_prev||^2: the rounding floor of the FP64 residual).  prev2 holds
-// ||r_prev||^2 (0 before the first sweep).  Counts sweeps in fl[FL_IRSWEEPS].
+// ||r_prev||^2 (0 before the first sweep).  After the first sweep the contraction is not yet
+// known from this solve: rho2 holds the last one measured (a property of the FP32 factor and
+// the matrix, the same for every right-hand side; 0 until measured) and, inflated by 4,
+// predicts the next correction.  Counts sweeps in fl[FL_IRSWEEPS].
 __global__ void k_ir_check(const double *x, const double *r, long long n, double eps2, double *partial,
-                           unsigned *counter, int *fl, double *prev2, double stag2) {
+                           unsigned *counter, int *fl, double *prev2, double stag2, double *rho2) {
   if (fl[FL_IRSKIP]) return;
   double sr = 0.0, sx = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -306,7 +309,9 @@ __global__ void k_ir_check(const double *x, const double *r, long long n, double
     for (int i = 0; i < (int)gridDim.x; ++i) t1 += ((volatile double *)partial)[i];
     fl[FL_IRSWEEPS] += 1;
     const double p2 = *prev2;
+    if (p2 > 0.0 && t1 < p2) *rho2 = t1 / p2;
     if (t1 <= eps2 * tx || !(t1 == t1) || (p2 > 0.0 && t1 * t1 <= eps2 * tx * p2) ||
+        (p2 == 0.0 && *rho2 > 0.0 && 4.0 * *rho2 * t1 <= eps2 * tx) ||
         (stag2 > 0.0 && p2 > 0.0 && t1 > stag2 * p2))
       fl[FL_IRSKIP] = 1;
     *prev2 = t1;
