@@ -28,6 +28,20 @@ sys.path.insert(0, ROOT)
 METRIC = "time steps/s at lambda rel. residual 1e-8"
 
 
+def job_rate(local_s, steps, world, device="cuda"):
+    """Whole-job rate of `world` independent replicas that each ran `steps` steps in
+    `local_s` seconds: the slowest rank bounds the job (MAX over ranks with
+    torch.distributed when world > 1).  Returns (steps per second of the job, job seconds)."""
+    job_s = float(local_s)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([job_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        job_s = float(t.item())
+    return world * steps / job_s, job_s
+
+
 def config5s():
     """Profiling case: the subdomains and physics of config 5 on a 16 x 16 partition
     (256 subdomains, about 3 GB of FP32 factors: larger than L2, small enough for ncu)."""
@@ -253,11 +267,8 @@ def run_native(args):
     ms = ev0.elapsed_time(ev1)
     kN, kD = sol.kernel_stats(0), sol.kernel_stats(1)
     sol.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1000.0)
+    value, job_s = job_rate(ms / 1000.0, args.steps, world)
+    ms = job_s * 1000.0
     # ---- end to end through the public API, host buffers ------------------------------
     s = sol.sizes
     lam_h = torch.empty(s.n_lambda, dtype=torch.float64).pin_memory().numpy()
@@ -271,11 +282,7 @@ def run_native(args):
         F._lib.fp_get_fields(sol._h, u_h.ctypes.data, f_h[0].ctypes.data, f_h[1].ctypes.data,
                              f_h[2].ctypes.data, 0)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_rate, e2e_s = job_rate(time.perf_counter() - t0, args.steps, world)
     d2h = 8 * (s.n_lambda + 2 * s.n_unode_total + 3 * s.n_pnode_total)
     # ---- roofline of the dominant kernel (banded local solves) -------------------------
     launches = kN["launches"] + kD["launches"]
@@ -322,7 +329,7 @@ def run_native(args):
                        "first_timed_step": (args.learned_record_steps if learned else 0) + args.warmup + 1,
                        "parallelism": "replicas (one independent problem per GPU)"},
             "roofline": roof, "clocks": clk,
-            "e2e": {"value": world * args.steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": e2e_rate, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": None}
     # kernel launches of the library in the timed region (counted from the loop structure)
