@@ -48,7 +48,7 @@ __global__ void k_pcg_update(double *, double *, const double *, const double *,
                              double *, int *);
 __global__ void k_pcg_pupdate(double *, const double *, long long, const double *, const int *);
 __global__ void k_lincomb(double *, const double *, double, const double *, double, long long, const int *);
-__global__ void k_scatter(DevTopo, const double *, double, double *, int, const int *);
+__global__ void k_scatter(DevTopo, const double *, double, double *, int, const int *, int);
 __global__ void k_gather(DevTopo, const double *, double *, const int *);
 __global__ void k_wscale(DevTopo, const double *, double *, const int *);
 __global__ void k_halo(DevTopo, const double *, const double *, double *, const int *);
@@ -632,13 +632,13 @@ fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
 double *xsol(fp_handle *h) { return h->P.precision == FP_PREC_MIXED ? h->XA : h->XB; }
 
 fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, bool accurate = true) {
-  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, v, 1.0, h->XB, 1, fl);
-  CKL();
   // explicit F_s: every apply in FP64, the loop's inexact apply in mixed precision (only the
   // rows touched by B are formed, so K^+ B^T v is not left in xsol)
   const bool mixed = h->P.precision == FP_PREC_MIXED;
   const void *op = nullptr;
   if (h->ops_ready) op = !mixed || !accurate ? h->opF : (h->opF64_ready ? h->opF64 : nullptr);
+  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, v, 1.0, h->XB, 1, fl, op ? 0 : 1);
+  CKL();
   if (op) {
     if (mixed && !accurate)
       CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)op, h->tile_off, h->XB, fl, h->stream));
@@ -672,7 +672,7 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
   }
   if (h->P.precond == FP_PRECOND_LUMPED) return apply_M_lumped(h, v, out, fl);
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
-  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl);
+  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl, h->ops_ready ? 0 : 1);
   CKL();
   if (h->ops_ready) {
     if (h->P.precision == FP_PREC_MIXED)
@@ -699,7 +699,7 @@ fp_status apply_M_lumped(fp_handle *h, const double *v, double *out, const int *
   const int nl = h->T.n_lambda;
   const int ng = (int)h->T.wgrp_first.size();
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
-  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl);
+  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl, 1);
   k_bnd_apply<<<h->T.S, 256, h->nbnd_max * sizeof(double), h->stream>>>(h->D, h->csr_val, nullptr, h->XP, fl);
   k_gather<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, h->t2, fl);
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, h->t2, out, fl);
@@ -1043,12 +1043,15 @@ fp_status build_explicit(fp_handle *h) {
   if (!h->opF64_ready) {
     st = run_mrhs(h, true, h->facN, h->linvN, 0, full);
     if (st == FP_OK && launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opF, h->tile_off,
-                                       h->stream) != cudaSuccess) { h->err = "pack"; st = FP_ERR_CUDA; }
+                                       h->stream) != cudaSuccess) {
+      h->err = "explicit operators: packing the symmetric tiles of F_s failed";
+      st = FP_ERR_CUDA;
+    }
   }
   if (st == FP_OK && need_S) st = run_mrhs(h, true, h->facD, h->linvD, 1, full);
   if (st == FP_OK && need_S &&
       launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opS, h->tile_off, h->stream) != cudaSuccess) {
-    h->err = "pack";
+    h->err = "explicit operators: packing the symmetric tiles of S_s failed";
     st = FP_ERR_CUDA;
   }
   const cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -1382,7 +1385,7 @@ fp_status step_recovery(fp_handle *h) {
   if (h->ops_ready && (h->P.precision == FP_PREC_FP64 || h->opF64_ready)) {
     // the explicit accurate apply formed only the interface rows of K^+ B^T lambda: one full
     // (refined) solve for the recovery
-    k_scatter<<<T.S, 256, 0, s>>>(h->D, h->lam, 1.0, h->XB, 1, nullptr);
+    k_scatter<<<T.S, 256, 0, s>>>(h->D, h->lam, 1.0, h->XB, 1, nullptr, 1);
     CKL();
     if (h->P.precision == FP_PREC_MIXED) TRY(solve_refined(h, h->XB, h->XA, h->ir_sweeps, nullptr));
     else TRY(solve_local(h, false, h->XB, nullptr));

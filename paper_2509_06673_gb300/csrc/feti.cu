@@ -144,18 +144,27 @@ __global__ void k_lincomb(double *out, const double *x, double a, const double *
 // ---------------------------------- jump operator -----------------------------------
 // Local vectors x_s = scale * B_s^T v on the dofs touched by B_s, zero elsewhere.
 // skip_fixed: leave the fixed dofs of floating subdomains at zero (K^+ convention).
-__global__ void k_scatter(DevTopo D, const double *v, double scale, double *xloc, int skip_fixed, const int *fl) {
+// zero_all: clear the whole local vector first (the band solves read every row); without it
+// only the rows touched by B are written (the explicit operators read nothing else), fixed
+// dofs of floating subdomains as 0
+__global__ void k_scatter(DevTopo D, const double *v, double scale, double *xloc, int skip_fixed, const int *fl,
+                          int zero_all) {
   if (fl && fl[FL_DONE]) return;
   const int s = blockIdx.x;
   const DevTpl t = D.tpl[D.sub_tpl[s]];
   double *x = xloc + D.vec_off[s];
-  for (int d = threadIdx.x; d < t.n; d += blockDim.x) x[d] = 0.0;
-  __syncthreads();
+  if (zero_all) {
+    for (int d = threadIdx.x; d < t.n; d += blockDim.x) x[d] = 0.0;
+    __syncthreads();
+  }
   const int *bnd = D.pool + t.bnd;
   const long long b0 = D.bsc_off[s];
   for (int q = threadIdx.x; q < t.nbnd; q += blockDim.x) {
     const int d = bnd[q];
-    if (skip_fixed && t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2)) continue;
+    if (skip_fixed && t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2)) {
+      x[d] = 0.0;
+      continue;
+    }
     double acc = 0.0;
 #pragma unroll
     for (int z = 0; z < 3; ++z) {
