@@ -7,7 +7,7 @@ relative projected residual of `tol`, and the recovery of (u, xi, eta, p).
 
 Arms
   native (default)   the CUDA library, one independent replica per GPU ("replicas only":
-                     the solve of one problem does not shard across GPUs in this build).
+                     the library solves one problem on one GPU).
   --impl reference   the CPU oracle (plain FP64 scipy FETI) on the host cores, on a bounded
                      sample of the same workload (a smaller partition of the same
                      subdomains), scaled to the full workload by the subdomain count.

@@ -118,7 +118,7 @@ typedef struct {
   double rel_residual;       /* recursive ||P r|| / ||P(d - F lambda_00)|| at exit */
   double true_rel_residual;  /* the same with r recomputed from lambda at exit */
   int lambda0_learned;       /* 1 if the learned guess moved lambda_0 off the lambda^{n-1} guess:
-                                the judge minimises the true residual over the span of lambda^{n-1},
+                                the guess selector minimises the true residual over the span of lambda^{n-1},
                                 the extrapolation and the network's correction (see
                                 fp_learned_use) */
   double guess_res_prev;     /* relative true residual of the lambda^{n-1} guess (-1: not computed) */
@@ -251,7 +251,7 @@ fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
  * extrapolation, in units of s = RMS(dl).  With fp_learned_use on, fp_step forms the
  * directions tc = P(rho dl) and tb = P(s MLP) from lambda_a = lambda_00 + P lambda^{n-1} and
  * takes lambda_0 = lambda_a + a tc + b tb with (a, b) minimising the true projected residual
- * ||P(d - F lambda_0)||_2 (the judge: a 2 x 2 least-squares problem, two more accurate F
+ * ||P(d - F lambda_0)||_2 (the guess selector: a 2 x 2 least-squares problem, two more accurate F
  * applications); (a, b) = (0, 0), the previous-step guess, is the fallback and never beaten
  * by the result.  Parameters: one flat FP32 array of
  * 68353 values: W1 [8 x 256] row-major, b1 [256], W2 [256 x 256] row-major, b2 [256],

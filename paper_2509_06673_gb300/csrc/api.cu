@@ -1195,7 +1195,7 @@ fp_status step_prologue(fp_handle *h, bool use_learned) {
   TRY(lincomb(h, h->r, h->d, 1.0, h->q, -1.0, nullptr));
   TRY(apply_P(h, h->r, h->r, h->fl_zero));
   // learned lambda_0: the network predicts a correction to the source-scaled extrapolation;
-  // the judge takes the point of smallest true projected residual on the affine span of
+  // the guess selector takes the point of smallest true projected residual on the affine span of
   // lambda_a = lambda_00 + P lambda^{n-1} (the fallback), the extrapolation and the network's
   // correction (two more accurate F applications).  nrm: [0] ||r_a||^2, [1] ||r_0||^2,
   // [2..6] the Gram entries, [7..8] the coefficients.

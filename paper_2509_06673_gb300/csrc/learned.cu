@@ -295,7 +295,7 @@ __global__ void k_gather_rows(int m, const int *idx, const float *SX, const floa
   else Y[i] = SY[s];
 }
 
-// The judge: lambda_0 = lambda_a + a tc + b tb with (a, b) minimising the true projected
+// The guess selector: lambda_0 = lambda_a + a tc + b tb with (a, b) minimising the true projected
 // residual ||r_a - a u - b w||_2 (u = P F tc, w = P F tb; the residual is affine in lambda),
 // from g = (u.u, u.w, w.w, u.r_a, w.r_a); (0, 0), the previous-step guess, is one of the
 // candidates, so the result is never worse.  One thread.

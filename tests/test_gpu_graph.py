@@ -107,7 +107,7 @@ def test_graph_loop_bounds(F):
 
 
 def test_graph_learned_matches_stream(F):
-    """The learned-guess variant of the step graph (features, MLP, judge inside the graph)."""
+    """The learned-guess variant of the step graph (features, MLP, guess selection inside the graph)."""
     case = W.small_case(4, 4, 4, k=2, lame_lambda=9.0, tau=2e-3, n_steps=12, tol=1e-8, source="point",
                         q_omega=25.0)
     case = case.with_(src_node=W.point_source_node(case, 1000))

@@ -72,7 +72,7 @@ def _point_case(seed_node, n_steps):
 def test_learned_guess_reduces_iterations(F):
     """Train on the steps of one source location, evaluate on another (unseen) location at
     the metric's tolerance 1e-8: the learned guess starts PCG from a much smaller true
-    residual than lambda^{n-1} and saves iterations; the judge keeps the solution exact."""
+    residual than lambda^{n-1} and saves iterations; the guess selector keeps the solution exact."""
     train = F.Solver(_point_case(1000, 80))
     train.assemble()
     train.factor()
@@ -107,6 +107,6 @@ def test_learned_guess_reduces_iterations(F):
     its0, _, lam0, _ = run(False)
     its1, wins, lam1, ratio = run(True)
     assert np.abs(lam1 - lam0).max() <= 1e-6 * np.abs(lam0).max()   # same solution (tol 1e-8)
-    assert wins >= 40                                                 # the network wins the judge
+    assert wins >= 40                                                 # the network wins the selection
     assert np.median(ratio) < 0.1, (np.median(ratio), its0.sum(), its1.sum())  # 10x smaller start
     assert its1[5:].sum() < 0.9 * its0[5:].sum(), (its0, its1)
