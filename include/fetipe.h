@@ -170,7 +170,8 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats);
  * (FP_ERR_STATE before). */
 fp_status fp_set_initial(fp_handle *h, const double *u0, const double *p0);
 
-/* Runs n_steps steps back to back (same as calling fp_step n_steps times). */
+/* Runs n_steps steps back to back (same as calling fp_step n_steps times); stops at the first
+ * step that does not return FP_OK and returns its status.  FP_ERR_INVALID for n_steps < 0. */
 fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last);
 
 fp_status fp_get_sizes(const fp_handle *h, fp_sizes *out);

@@ -1673,6 +1673,7 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
 }
 
 fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last) {
+  if (!h || n_steps < 0) return FP_ERR_INVALID;
   for (int i = 0; i < n_steps; ++i) {
     fp_status st = fp_step(h, last);
     if (st) return st;

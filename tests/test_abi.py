@@ -46,3 +46,51 @@ def test_invalid_input_rejected_on_host(lib):
     with pytest.raises(F.FetipeError) as e:
         F.Solver(bad)
     assert e.value.status == 1 and "point source" in str(e.value)
+
+
+_CTYPE = {"int": ctypes.c_int, "long long": ctypes.c_longlong,
+          "unsigned long long": ctypes.c_ulonglong, "double": ctypes.c_double}
+
+
+def _signatures():
+    src = open(os.path.join(ROOT, "include", "fetipe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"(fp_status|const char \*|void)\s*(fp_\w+)\s*\(([^)]*)\)\s*;", src):
+        args = []
+        for a in m.group(3).split(","):
+            a = " ".join(a.split())
+            if "*" in a:
+                args.append(ctypes.c_void_p)
+            else:
+                args.append(_CTYPE[a.rsplit(" ", 1)[0].replace("const ", "")])
+        out[m.group(2)] = (m.group(1), args)
+    return out
+
+
+def test_null_handle_rejected_without_gpu(lib):
+    """Every call that takes a handle returns FP_ERR_INVALID (1) for a NULL handle before it
+    touches the device; fp_create rejects NULL arguments; fp_destroy(NULL) is a no-op and
+    fp_last_error(NULL) reports the last fp_create failure."""
+    sigs = _signatures()
+    assert len(sigs) == len(_declared())
+    for name, (ret, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        zeros = [None if a is ctypes.c_void_p else a(0) for a in args]
+        if name == "fp_destroy":
+            fn.restype = None
+            fn(*zeros)
+        elif name == "fp_last_error":
+            fn.restype = ctypes.c_char_p
+            assert fn(None) is not None
+        elif name == "fp_create":
+            fn.restype = ctypes.c_int
+            assert fn(None, None, None, None) == 1
+            out = ctypes.c_void_p(1)
+            assert fn(None, None, None, ctypes.byref(out)) == 1 and out.value is None
+        else:
+            fn.restype = ctypes.c_int
+            if name == "fp_run":
+                zeros[1] = ctypes.c_int(1)
+            assert fn(*zeros) == 1, name
