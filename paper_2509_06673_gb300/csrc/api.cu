@@ -1479,11 +1479,27 @@ fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cud
   if (params->perm) {
     h->perm.assign(params->perm, params->perm + h->T.elem_off[h->T.S]);
     for (double v : h->perm)
-      if (!(v > 0) || !std::isfinite(v)) { delete h; return FP_ERR_INVALID; }
+      if (!(v > 0) || !std::isfinite(v)) {
+        g_create_err = "fp_create: perm values must be positive and finite";
+        delete h;
+        return FP_ERR_INVALID;
+      }
   }
   h->P.perm = nullptr;
   h->stream = (cudaStream_t)cuda_stream;
-  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return FP_ERR_CUDA; }
+  {
+    // no host fallback: without a usable CUDA device the call fails
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce == cudaSuccess && ndev < 1) ce = cudaErrorNoDevice;
+    if (ce == cudaSuccess) ce = cudaGetDevice(&h->device);
+    if (ce != cudaSuccess) {
+      g_create_err = std::string("fp_create: no usable CUDA device (") + cudaGetErrorString(ce) + ")";
+      cudaGetLastError();
+      delete h;
+      return FP_ERR_CUDA;
+    }
+  }
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   fp_status st = build_device(h);
   if (st != FP_OK) { g_create_err = h->err; fp_destroy(h); return st; }

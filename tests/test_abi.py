@@ -94,3 +94,28 @@ def test_null_handle_rejected_without_gpu(lib):
             if name == "fp_run":
                 zeros[1] = ctypes.c_int(1)
             assert fn(*zeros) == 1, name
+
+
+def test_bad_permeability_rejected_on_host(lib):
+    from paper_2509_06673_gb300 import fetipe as F
+    from paper_2509_06673_gb300 import workloads as W
+    case = W.small_case(2, 2, 4)
+    case = case.with_(perm=W.lognormal_perm(case, sigma=1.0, seed=3))
+    case.perm[1] = case.perm[1].copy()
+    case.perm[1][5] = -1.0
+    with pytest.raises(F.FetipeError) as e:
+        F.Solver(case)
+    assert e.value.status == 1 and "perm" in str(e.value)
+
+
+def test_no_host_fallback_without_gpu(lib):
+    """A valid problem on a host without a CUDA device fails loudly (FP_ERR_CUDA): the
+    library has no CPU path."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2509_06673_gb300 import fetipe as F
+    from paper_2509_06673_gb300 import workloads as W
+    with pytest.raises(F.FetipeError) as e:
+        F.Solver(W.small_case(2, 2, 4))
+    assert e.value.status == 3 and "no usable CUDA device" in str(e.value)
