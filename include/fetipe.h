@@ -65,9 +65,9 @@ enum { FP_PRECOND_DIRICHLET = 0, FP_PRECOND_LUMPED = 1, FP_PRECOND_NONE = 2, FP_
  * boundary of Omega^P (no-flux on y = 1/2, Eq. (2.14)).
  */
 typedef struct {
-  int nsub_x, nsub_y;
-  const int *cells_x;   /* [nsub_x], each >= 1 */
-  const int *cells_y;   /* [nsub_y], each >= 1 */
+  int nsub_x, nsub_y;   /* 1 <= nsub_x <= 4096, 2 <= nsub_y <= 4096 */
+  const int *cells_x;   /* [nsub_x], each in [1, 4096] */
+  const int *cells_y;   /* [nsub_y], each in [1, 4096] */
   int poro_rows;        /* 1 <= poro_rows < nsub_y */
   int order_k;          /* 1 or 2 */
 } fp_mesh_desc;
@@ -129,8 +129,10 @@ typedef struct {
 
 /* Copies the mesh description and parameters, builds the dof numbering, band ordering and
  * interface tables on the host and uploads them to the current device.
- * cuda_stream: a cudaStream_t (NULL = default stream).  Errors: FP_ERR_INVALID, FP_ERR_OOM,
- * FP_ERR_CUDA.  *out is NULL on error. */
+ * cuda_stream: a cudaStream_t (NULL = default stream).  Errors: FP_ERR_INVALID (bad mesh or
+ * parameters), FP_ERR_OOM (host or device allocation), FP_ERR_CUDA (no usable device, or a
+ * CUDA call failed; there is no host fallback).  *out is NULL on error; fp_last_error(NULL)
+ * gives the message. */
 fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cuda_stream,
                     fp_handle **out);
 

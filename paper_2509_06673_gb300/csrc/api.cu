@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <new>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1471,7 +1472,15 @@ fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cud
     return FP_ERR_INVALID;
   }
   std::string err;
-  if (!build_topology(mesh, params, h->T, err)) {
+  bool topo_ok = false;
+  try {
+    topo_ok = build_topology(mesh, params, h->T, err);
+  } catch (const std::bad_alloc &) {
+    g_create_err = "fp_create: host allocation failed while building the topology";
+    delete h;
+    return FP_ERR_OOM;
+  }
+  if (!topo_ok) {
     g_create_err = "fp_create: " + err;
     delete h;
     return FP_ERR_INVALID;
@@ -1501,7 +1510,13 @@ fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cud
     }
   }
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-  fp_status st = build_device(h);
+  fp_status st;
+  try {
+    st = build_device(h);
+  } catch (const std::bad_alloc &) {
+    h->err = "fp_create: host allocation failed while building the device data";
+    st = FP_ERR_OOM;
+  }
   if (st != FP_OK) { g_create_err = h->err; fp_destroy(h); return st; }
   {
     const double esz = h->P.precision == FP_PREC_MIXED ? 4.0 : 8.0;

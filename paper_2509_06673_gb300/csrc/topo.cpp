@@ -213,6 +213,8 @@ struct NodeEnt { int s, d0, d1; };
 bool build_topology(const fp_mesh_desc *m, const fp_params *p, Topology &T, std::string &err) {
   if (!m || !p) { err = "null mesh or params"; return false; }
   if (m->nsub_x < 1 || m->nsub_y < 2 || !m->cells_x || !m->cells_y) { err = "bad partition"; return false; }
+  // global node indices (k * sum of cells + 1 per direction) and the subdomain count stay in int
+  if (m->nsub_x > 4096 || m->nsub_y > 4096) { err = "nsub_x and nsub_y must be at most 4096"; return false; }
   if (m->order_k != 1 && m->order_k != 2) { err = "order_k must be 1 or 2"; return false; }
   if (m->poro_rows < 1 || m->poro_rows >= m->nsub_y) { err = "poro_rows must be in [1, nsub_y)"; return false; }
   T.nsx = m->nsub_x; T.nsy = m->nsub_y; T.poro_rows = m->poro_rows; T.k = m->order_k;

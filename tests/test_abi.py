@@ -119,3 +119,15 @@ def test_no_host_fallback_without_gpu(lib):
     with pytest.raises(F.FetipeError) as e:
         F.Solver(W.small_case(2, 2, 4))
     assert e.value.status == 3 and "no usable CUDA device" in str(e.value)
+
+
+def test_partition_limits_rejected_on_host(lib):
+    from paper_2509_06673_gb300 import fetipe as F
+    from paper_2509_06673_gb300 import workloads as W
+    for bad, word in ((W.small_case(2, 2, 4).with_(cells_x=[4, 0]), "cells_x"),
+                      (W.small_case(2, 2, 4).with_(cells_y=[4, 5000]), "cells_y"),
+                      (W.small_case(2, 2, 4).with_(poro_rows=2), "poro_rows"),
+                      (W.small_case(5000, 2, 1), "4096")):
+        with pytest.raises(F.FetipeError) as e:
+            F.Solver(bad)
+        assert e.value.status == 1 and word in str(e.value), (word, str(e.value))
