@@ -1822,7 +1822,13 @@ fp_status fp_checkpoint(const fp_handle *hc, const char *path) {
   std::vector<unsigned char> buf;
   for (const CkptArray &a : ckpt_arrays(h)) {
     if (!ok) break;
-    buf.resize(a.bytes);
+    try {
+      buf.resize(a.bytes);
+    } catch (const std::bad_alloc &) {
+      std::fclose(f);
+      h->err = "fp_checkpoint: host allocation failed";
+      return FP_ERR_OOM;
+    }
     if (a.bytes && cudaMemcpy(buf.data(), a.dev, a.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
       std::fclose(f);
       h->err = "fp_checkpoint: device read failed";
@@ -1851,14 +1857,22 @@ fp_status fp_restore(fp_handle *h, const char *path) {
   }
   std::vector<std::vector<unsigned char>> data;
   for (const CkptArray &a : ckpt_arrays(h)) {
-    data.emplace_back(a.bytes);
+    try {
+      data.emplace_back(a.bytes);
+    } catch (const std::bad_alloc &) {
+      std::fclose(f);
+      h->err = "fp_restore: host allocation failed";
+      return FP_ERR_OOM;
+    }
     if (a.bytes && std::fread(data.back().data(), 1, a.bytes, f) != a.bytes) {
       std::fclose(f);
       h->err = "fp_restore: file truncated";
       return FP_ERR_INVALID;
     }
   }
+  const bool trailing = std::fgetc(f) != EOF;
   std::fclose(f);
+  if (trailing) { h->err = "fp_restore: bytes after the last array (not a checkpoint of this problem)"; return FP_ERR_INVALID; }
   const auto arrays = ckpt_arrays(h);
   CK(cudaStreamSynchronize(h->stream));
   for (size_t i = 0; i < arrays.size(); ++i)

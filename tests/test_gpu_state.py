@@ -92,6 +92,19 @@ def test_restore_rejects_other_problem(F, tmp_path):
     with pytest.raises(F.FetipeError):
         s2.restore(tmp_path / "bad")
     s2.close()
+    # same problem: a truncated file and one with bytes appended are rejected, the file
+    # itself is accepted
+    good = (tmp_path / "c1").read_bytes()
+    (tmp_path / "short").write_bytes(good[:-1])
+    (tmp_path / "long").write_bytes(good + b"\0")
+    s3 = F.Solver(c1)
+    s3.assemble()
+    for name in ("short", "long"):
+        with pytest.raises(F.FetipeError) as e:
+            s3.restore(tmp_path / name)
+        assert e.value.status == F.FP_ERR_INVALID, name
+    s3.restore(tmp_path / "c1")
+    s3.close()
 
 
 def test_set_initial_matches_oracle(F):
