@@ -7,7 +7,8 @@ mean-squared-error loss L = mean((out - y)^2) / 2 ... computed here in FP64.
 ``bf16_points=True`` rounds the operands of the two 256-wide products (h1 and W2 in the
 forward pass; the gradient d2 and W2, h1 and d2 in the backward pass) to bfloat16 with
 round-to-nearest-even, which is where the GPU feeds its tensor cores; everything else stays
-FP64.  Pinned by tests/test_oracle_mlp.py against central finite differences (FP64 mode).
+FP64.  Pinned by tests/test_oracle_mlp.py against central finite differences (FP64 mode), against
+torch.nn layers with autograd (FP64) and, for the rounding, against torch's bfloat16 conversion.
 
 Parameter vector layout (shared by both sides, as the ABI's flat parameter array):
 W1 [8 x 256] row-major, b1 [256], W2 [256 x 256] row-major, b2 [256], W3 [256], b3 [1].
