@@ -178,6 +178,15 @@ fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last);
 
 fp_status fp_get_sizes(const fp_handle *h, fp_sizes *out);
 
+/* Host-only planning: validates mesh and params as fp_create does, builds the dof numbering
+ * and interface tables on the host and reports the sizes fp_get_sizes would report for that
+ * problem (factor_bytes: the device bytes of the local factors at params->precision), without
+ * any CUDA call, so a problem can be sized against device memory before fp_create.
+ * lambda_keys: NULL, or [6 * n_lambda] ints that receive the key of every multiplier row in
+ * the format and order of fp_get_lambda_keys (call once with NULL to learn n_lambda).
+ * Errors: FP_ERR_INVALID, FP_ERR_OOM; fp_last_error(NULL) gives the message. */
+fp_status fp_plan(const fp_mesh_desc *mesh, const fp_params *params, fp_sizes *out, int *lambda_keys);
+
 /* lambda^n of the last step, n_lambda doubles.  Multiplier r enforces
  * x_{s_a} - x_{s_b} = 0 on one node component (see fp_get_lambda_keys). */
 fp_status fp_get_lambda(const fp_handle *h, double *dst, int on_device);

@@ -1452,6 +1452,31 @@ fp_status capture_step(fp_handle *h, bool use_learned) {
 }  // namespace
 
 // ====================================== ABI ==========================================
+// Parameter checks shared by fp_create and fp_plan (precond AUTO already mapped or not).
+static bool params_valid(const fp_params &P) {
+  return P.lame_lambda > 0 && P.mu > 0 && P.c0 > 0 && P.tau > 0 && P.mu_f > 0 && P.alpha >= 0 && P.tol > 0 &&
+         P.max_it >= 1 && (P.precision == FP_PREC_FP64 || P.precision == FP_PREC_MIXED) &&
+         P.precond >= FP_PRECOND_DIRICHLET && P.precond <= FP_PRECOND_AUTO;
+}
+
+static bool perm_valid(const double *perm, long long n) {
+  for (long long e = 0; e < n; ++e)
+    if (!(perm[e] > 0) || !std::isfinite(perm[e])) return false;
+  return true;
+}
+
+static void sizes_of(const Topology &T, int precision, fp_sizes *o) {
+  o->nsub = T.S; o->n_floating = T.NF; o->n_lambda = T.n_lambda; o->n_lambda_p = T.n_lambda_p;
+  long long nd = 0;
+  int bmax = 0;
+  for (int s = 0; s < T.S; ++s) { nd += T.tpl[T.sub_tpl[s]].n; bmax = std::max(bmax, T.tpl[T.sub_tpl[s]].b); }
+  o->n_dofs = nd;
+  o->n_unode_total = T.unode_off[T.S];
+  o->n_pnode_total = T.pnode_off[T.S];
+  o->factor_bytes = 2LL * T.fac_off[T.S] * (precision == FP_PREC_MIXED ? 4 : 8);
+  o->max_half_band = bmax;
+}
+
 extern "C" {
 
 fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cuda_stream, fp_handle **out) {
@@ -1463,10 +1488,7 @@ fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cud
   h->P = *params;
   h->precond_req = h->P.precond;
   if (h->P.precond == FP_PRECOND_AUTO) h->P.precond = FP_PRECOND_DIRICHLET;
-  if (!(h->P.lame_lambda > 0) || !(h->P.mu > 0) || !(h->P.c0 > 0) || !(h->P.tau > 0) || !(h->P.mu_f > 0) ||
-      !(h->P.alpha >= 0) || !(h->P.tol > 0) || h->P.max_it < 1 ||
-      (h->P.precision != FP_PREC_FP64 && h->P.precision != FP_PREC_MIXED) ||
-      h->P.precond < FP_PRECOND_DIRICHLET || h->P.precond > FP_PRECOND_AUTO) {
+  if (!params_valid(h->P)) {
     g_create_err = "fp_create: invalid parameters";
     delete h;
     return FP_ERR_INVALID;
@@ -1486,13 +1508,12 @@ fp_status fp_create(const fp_mesh_desc *mesh, const fp_params *params, void *cud
     return FP_ERR_INVALID;
   }
   if (params->perm) {
+    if (!perm_valid(params->perm, h->T.elem_off[h->T.S])) {
+      g_create_err = "fp_create: perm values must be positive and finite";
+      delete h;
+      return FP_ERR_INVALID;
+    }
     h->perm.assign(params->perm, params->perm + h->T.elem_off[h->T.S]);
-    for (double v : h->perm)
-      if (!(v > 0) || !std::isfinite(v)) {
-        g_create_err = "fp_create: perm values must be positive and finite";
-        delete h;
-        return FP_ERR_INVALID;
-      }
   }
   h->P.perm = nullptr;
   h->stream = (cudaStream_t)cuda_stream;
@@ -1714,16 +1735,28 @@ fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last) {
 
 fp_status fp_get_sizes(const fp_handle *h, fp_sizes *o) {
   if (!h || !o) return FP_ERR_INVALID;
-  const Topology &T = h->T;
-  o->nsub = T.S; o->n_floating = T.NF; o->n_lambda = T.n_lambda; o->n_lambda_p = T.n_lambda_p;
-  long long nd = 0;
-  int bmax = 0;
-  for (int s = 0; s < T.S; ++s) { nd += T.tpl[T.sub_tpl[s]].n; bmax = std::max(bmax, T.tpl[T.sub_tpl[s]].b); }
-  o->n_dofs = nd;
-  o->n_unode_total = T.unode_off[T.S];
-  o->n_pnode_total = T.pnode_off[T.S];
-  o->factor_bytes = 2LL * T.fac_off[T.S] * (h->P.precision == FP_PREC_MIXED ? 4 : 8);
-  o->max_half_band = bmax;
+  sizes_of(h->T, h->P.precision, o);
+  return FP_OK;
+}
+
+fp_status fp_plan(const fp_mesh_desc *mesh, const fp_params *params, fp_sizes *out, int *lambda_keys) {
+  if (!mesh || !params || !out) { g_create_err = "fp_plan: null argument"; return FP_ERR_INVALID; }
+  if (!params_valid(*params)) { g_create_err = "fp_plan: invalid parameters"; return FP_ERR_INVALID; }
+  try {
+    Topology T;
+    std::string err;
+    if (!build_topology(mesh, params, T, err)) { g_create_err = "fp_plan: " + err; return FP_ERR_INVALID; }
+    if (params->perm && !perm_valid(params->perm, T.elem_off[T.S])) {
+      g_create_err = "fp_plan: perm values must be positive and finite";
+      return FP_ERR_INVALID;
+    }
+    sizes_of(T, params->precision, out);
+    if (lambda_keys && T.n_lambda)
+      std::memcpy(lambda_keys, T.lam_key.data(), (size_t)6 * T.n_lambda * sizeof(int));
+  } catch (const std::bad_alloc &) {
+    g_create_err = "fp_plan: host allocation failed";
+    return FP_ERR_OOM;
+  }
   return FP_OK;
 }
 

@@ -4,7 +4,8 @@ CPU fallback.
 
 Names follow the C ABI of include/fetipe.h: ``create``, ``assemble``, ``factor``, ``step``,
 ``run``, ``get_lambda``, ``get_lambda_keys``, ``get_fields``, ``apply_F``,
-``apply_precond``, ``apply_projection``, ``get_dof_map``, ``get_local_matrix``.
+``apply_precond``, ``apply_projection``, ``get_dof_map``, ``get_local_matrix``, and ``plan``
+(fp_plan: sizes and multiplier keys from the library's host topology builder, no device).
 """
 import ctypes
 import os
@@ -27,7 +28,7 @@ FP_SOURCE_MANUFACTURED, FP_SOURCE_POINT, FP_SOURCE_MANUFACTURED_T = 0, 1, 2
 FP_PREC_FP64, FP_PREC_MIXED = 0, 1
 FP_PRECOND_DIRICHLET, FP_PRECOND_LUMPED, FP_PRECOND_NONE, FP_PRECOND_AUTO = 0, 1, 2, 3
 
-EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_get_sizes",
+EXPORTED = ["fp_create", "fp_assemble", "fp_factor", "fp_step", "fp_run", "fp_get_sizes", "fp_plan",
             "fp_get_lambda", "fp_get_lambda_keys", "fp_get_fields", "fp_get_subdomain", "fp_set_initial",
             "fp_checkpoint", "fp_restore", "fp_apply_F",
             "fp_apply_precond", "fp_apply_projection", "fp_apply_projection_noalloc",
@@ -90,6 +91,7 @@ for _n in ("fp_assemble", "fp_factor"):
 _lib.fp_step.argtypes = [_vp, ctypes.POINTER(StepStats)]
 _lib.fp_run.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(StepStats)]
 _lib.fp_get_sizes.argtypes = [_vp, ctypes.POINTER(Sizes)]
+_lib.fp_plan.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), ctypes.POINTER(Sizes), _vp]
 _lib.fp_get_lambda.argtypes = [_vp, _vp, ctypes.c_int]
 _lib.fp_get_lambda_keys.argtypes = [_vp, _vp]
 _lib.fp_get_fields.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
@@ -137,30 +139,53 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _describe(case, precision=None):
+    """(fp_mesh_desc, fp_params, arrays that must outlive the call) for a workloads.Case."""
+    cx = np.ascontiguousarray(case.cells_x, dtype=np.int32)
+    cy = np.ascontiguousarray(case.cells_y, dtype=np.int32)
+    keep = [cx, cy]
+    mesh = MeshDesc(case.nsub_x, case.nsub_y, cx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                    cy.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), case.poro_rows, case.order_k)
+    perm_ptr = None
+    if case.perm is not None:
+        perm = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in case.perm]))
+        keep.append(perm)
+        perm_ptr = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    src = {"manufactured": FP_SOURCE_MANUFACTURED, "point": FP_SOURCE_POINT,
+           "manufactured_t": FP_SOURCE_MANUFACTURED_T}[case.source]
+    prec = precision or case.precision
+    par = Params(case.lame_lambda, case.mu, case.alpha, case.c0, case.perm_k, case.mu_f, case.tau,
+                 perm_ptr, src, int(case.src_node[0]), int(case.src_node[1]), float(case.q_omega),
+                 FP_PREC_MIXED if prec == "mixed" else FP_PREC_FP64,
+                 {"dirichlet": FP_PRECOND_DIRICHLET, "lumped": FP_PRECOND_LUMPED, "none": FP_PRECOND_NONE,
+                  "auto": FP_PRECOND_AUTO}[case.precond],
+                 case.tol, case.max_it)
+    return mesh, par, keep
+
+
+def plan(case, precision=None, keys=False):
+    """fp_plan: the sizes of ``case`` (and, with keys=True, its multiplier keys as an
+    (n_lambda, 6) int32 array) computed on the host, without a CUDA device."""
+    mesh, par, keep = _describe(case, precision)
+    s = Sizes()
+    st = _lib.fp_plan(ctypes.byref(mesh), ctypes.byref(par), ctypes.byref(s), None)
+    if st != FP_OK:
+        raise FetipeError(st, _lib.fp_last_error(None).decode())
+    if not keys:
+        return s
+    k = np.empty((s.n_lambda, 6), dtype=np.int32)
+    st = _lib.fp_plan(ctypes.byref(mesh), ctypes.byref(par), ctypes.byref(s), k.ctypes.data)
+    if st != FP_OK:
+        raise FetipeError(st, _lib.fp_last_error(None).decode())
+    return s, k
+
+
 class Solver:
     """One fetipe handle.  ``case`` is a workloads.Case."""
 
     def __init__(self, case, stream=None, precision=None):
         self._h = _vp()
-        cx = np.ascontiguousarray(case.cells_x, dtype=np.int32)
-        cy = np.ascontiguousarray(case.cells_y, dtype=np.int32)
-        self._keep = [cx, cy]
-        mesh = MeshDesc(case.nsub_x, case.nsub_y, cx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                        cy.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), case.poro_rows, case.order_k)
-        perm_ptr = None
-        if case.perm is not None:
-            perm = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in case.perm]))
-            self._keep.append(perm)
-            perm_ptr = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        src = {"manufactured": FP_SOURCE_MANUFACTURED, "point": FP_SOURCE_POINT,
-               "manufactured_t": FP_SOURCE_MANUFACTURED_T}[case.source]
-        prec = precision or case.precision
-        par = Params(case.lame_lambda, case.mu, case.alpha, case.c0, case.perm_k, case.mu_f, case.tau,
-                     perm_ptr, src, int(case.src_node[0]), int(case.src_node[1]), float(case.q_omega),
-                     FP_PREC_MIXED if prec == "mixed" else FP_PREC_FP64,
-                     {"dirichlet": FP_PRECOND_DIRICHLET, "lumped": FP_PRECOND_LUMPED, "none": FP_PRECOND_NONE,
-                      "auto": FP_PRECOND_AUTO}[case.precond],
-                     case.tol, case.max_it)
+        mesh, par, self._keep = _describe(case, precision)
         st = _lib.fp_create(ctypes.byref(mesh), ctypes.byref(par), stream, ctypes.byref(self._h))
         if st != FP_OK:
             raise FetipeError(st, _lib.fp_last_error(None).decode())
