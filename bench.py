@@ -274,16 +274,22 @@ def run_native(args):
     lam_h = torch.empty(s.n_lambda, dtype=torch.float64).pin_memory().numpy()
     u_h = torch.empty(2 * s.n_unode_total, dtype=torch.float64).pin_memory().numpy()
     f_h = [torch.empty(s.n_pnode_total, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    xfer = [0, 0]
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        sol.step()
+        st = sol.step()
         sol.get_lambda(lam_h)
         F._lib.fp_get_fields(sol._h, u_h.ctypes.data, f_h[0].ctypes.data, f_h[1].ctypes.data,
                              f_h[2].ctypes.data, 0)
+        xfer[0] += st["h2d_bytes"]
+        xfer[1] += st["d2h_bytes"]
     barrier()
     e2e_rate, e2e_s = job_rate(time.perf_counter() - t0, args.steps, world)
-    d2h = 8 * (s.n_lambda + 2 * s.n_unode_total + 3 * s.n_pnode_total)
+    # per step: the library's own scalar and flag copies (reported by fp_step) plus the
+    # caller's read of lambda and all fields
+    h2d = xfer[0] // args.steps
+    d2h = xfer[1] // args.steps + 8 * (s.n_lambda + 2 * s.n_unode_total + 3 * s.n_pnode_total)
     # ---- roofline of the dominant kernel (banded local solves) -------------------------
     launches = kN["launches"] + kD["launches"]
     avg_ms = (kN["total_ms"] + kD["total_ms"]) / max(launches, 1)
@@ -329,8 +335,11 @@ def run_native(args):
                        "first_timed_step": (args.learned_record_steps if learned else 0) + args.warmup + 1,
                        "parallelism": "replicas (one independent problem per GPU)"},
             "roofline": roof, "clocks": clk,
-            "e2e": {"value": e2e_rate, "unit": "steps/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_rate, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "inputs": "per-step inputs are the time level and the loop settings copied from "
+                              "pinned host memory; the sources are closed-form functions of (x, t) "
+                              "evaluated by the library on the device"},
             "gpu_launches": None}
     # kernel launches of the library in the timed region, from the loop structure (the ncu launch
     # list of the explicit-operator step: about 21 per PCG iteration and 155 per step outside it)

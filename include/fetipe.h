@@ -125,6 +125,9 @@ typedef struct {
   double guess_res_learned;  /* relative true residual of the learned lambda_0 (-1: not computed) */
   int restarts;              /* restarts of Algorithm 1 from the true residual */
   int stagnations;           /* rounds stopped because the recursive residual stalled */
+  long long h2d_bytes;       /* host -> device bytes the step copied (per-step scalars, loop flags) */
+  long long d2h_bytes;       /* device -> host bytes the step copied (loop flags, scalars, status);
+                                the caller's fp_get_* reads are not included */
 } fp_step_stats;
 
 /* Copies the mesh description and parameters, builds the dof numbering, band ordering and

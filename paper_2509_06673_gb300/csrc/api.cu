@@ -172,6 +172,7 @@ struct fp_handle {
   std::vector<cudaEvent_t> gev;  // events recorded by the graph (profiling)
   size_t gev_used = 0;
   double *stepv = nullptr, *h_stepv = nullptr;  // per-step scalars (device, pinned host)
+  long long xfer[2] = {0, 0};                    // host->device, device->host bytes of the last fp_step
   int *h_flinit = nullptr;                      // initial PCG flags (pinned host)
   double *lam = nullptr, *lam_prev = nullptr, *lam00 = nullptr, *d = nullptr, *r = nullptr, *z = nullptr,
          *p = nullptr, *q = nullptr, *t1 = nullptr, *t2 = nullptr;
@@ -1278,12 +1279,14 @@ fp_status krylov_stream(fp_handle *h, int *restarts_out) {
     for (int it = 0; it < h->P.max_it; it += h->pcg_chunk) {
       for (int c = 0; c < h->pcg_chunk; ++c) TRY(pcg_iteration(h));
       CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
+      h->xfer[1] += FL_N * sizeof(int);
       CK(cudaStreamSynchronize(s));
       if (h->h_fl[FL_DONE]) break;
     }
     TRY(true_residual(h));
     CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    h->xfer[1] += FL_N * sizeof(int) + SC_N * sizeof(double);
     CK(cudaStreamSynchronize(s));
     const bool ok = h->h_sc[SC_TRUE2] <= tol2 * h->h_sc[SC_REF2];
     if (ok || h->h_fl[FL_STATUS] || restarts >= h->max_restarts || h->h_fl[FL_ITER] >= h->P.max_it) break;
@@ -1650,6 +1653,10 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   h->h_flinit[FL_STAGWIN] = h->stag_window;
   const bool use_learned = h->learned_use && h->mlp_ready && h->hist >= 2;
   int restarts = 0;
+  // the prologue copies the per-step scalars and the initial loop flags from pinned memory
+  // (graph path: as memcpy nodes replayed every launch)
+  h->xfer[0] = ST_N * sizeof(double) + FL_N * sizeof(int);
+  h->xfer[1] = 0;
   if (h->use_graph) {
     if (!h->gexec || h->gdirty || h->gkey != (use_learned ? 1 : 0)) TRY(capture_step(h, use_learned));
     CK(cudaEventRecord(h->ev[0], s));
@@ -1685,11 +1692,13 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
   CK(cudaEventRecord(h->ev[3], s));
   CK(cudaMemcpyAsync(h->h_fl, h->fl, FL_N * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_sc, h->sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  h->xfer[1] += FL_N * sizeof(int) + SC_N * sizeof(double) + sizeof(int);  // + the status word below
   double hn[2] = {-1, -1};
   int hflag = 0;
   if (use_learned) {
     CK(cudaMemcpyAsync(hn, h->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&hflag, h->choose_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    h->xfer[1] += 2 * sizeof(double) + sizeof(int);
   }
   CK(cudaStreamSynchronize(s));
   TRY(collect_profile(h));
@@ -1715,6 +1724,8 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
     stats->true_rel_residual = ref2 > 0 ? std::sqrt(h->h_sc[SC_TRUE2] / ref2) : 0.0;
     stats->restarts = restarts;
     stats->stagnations = h->h_fl[FL_NSTAG];
+    stats->h2d_bytes = h->xfer[0];
+    stats->d2h_bytes = h->xfer[1];
   }
   fp_status st = check_status(h);
   if (st) return st;

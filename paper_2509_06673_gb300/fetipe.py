@@ -81,7 +81,8 @@ class StepStats(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
                 ("lambda0_learned", ctypes.c_int), ("guess_res_prev", ctypes.c_double),
                 ("guess_res_learned", ctypes.c_double), ("restarts", ctypes.c_int),
-                ("stagnations", ctypes.c_int)]
+                ("stagnations", ctypes.c_int), ("h2d_bytes", ctypes.c_longlong),
+                ("d2h_bytes", ctypes.c_longlong)]
 
 
 _vp = ctypes.c_void_p
@@ -225,7 +226,7 @@ class Solver:
                 "rel_residual": st.rel_residual, "true_rel_residual": st.true_rel_residual,
                 "lambda0_learned": st.lambda0_learned, "guess_res_prev": st.guess_res_prev,
                 "guess_res_learned": st.guess_res_learned, "restarts": st.restarts,
-                "stagnations": st.stagnations}
+                "stagnations": st.stagnations, "h2d_bytes": st.h2d_bytes, "d2h_bytes": st.d2h_bytes}
 
     def run(self, n_steps):
         st = StepStats()

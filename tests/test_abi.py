@@ -131,3 +131,58 @@ def test_partition_limits_rejected_on_host(lib):
         with pytest.raises(F.FetipeError) as e:
             F.Solver(bad)
         assert e.value.status == 1 and word in str(e.value), (word, str(e.value))
+
+
+_STRUCTS = {"fp_mesh_desc": "MeshDesc", "fp_params": "Params", "fp_sizes": "Sizes",
+            "fp_step_stats": "StepStats", "fp_kernel_stats": "KernelStats", "fp_tuning": "Tuning"}
+
+
+def _header_structs():
+    """{struct name: [field names in order]} from the typedefs of include/fetipe.h."""
+    src = open(os.path.join(ROOT, "include", "fetipe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        names = []
+        for decl in m.group(1).split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            first = re.match(r"(?:const\s+)?(?:unsigned\s+)?(?:long long|int|double|float|char)\s*\**\s*", decl)
+            for d in decl[first.end():].split(","):
+                names.append(re.match(r"\s*\**\s*(\w+)", d).group(1))
+        out[m.group(2)] = names
+    return out
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every struct of include/fetipe.h has, in the ctypes binding, the same fields in the same
+    order at the offsets and with the total size that the C compiler gives (gcc, this host)."""
+    import shutil
+    import subprocess
+    from paper_2509_06673_gb300 import fetipe
+    structs = _header_structs()
+    assert set(structs) == set(_STRUCTS)
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fetipe.h"', "int main(void) {"]
+    for cname, fields in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in fields:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    (tmp_path / "layout.c").write_text("\n".join(lines))
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(tmp_path / "layout"),
+                    str(tmp_path / "layout.c")], check=True)
+    got = subprocess.run([str(tmp_path / "layout")], check=True, capture_output=True, text=True).stdout.split("\n")
+    c = {}
+    for ln in got:
+        if ln:
+            a, b, v = ln.split()
+            c[(a, b)] = int(v)
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(fetipe, pyname)
+        assert [f[0] for f in cls._fields_] == structs[cname], cname
+        assert ctypes.sizeof(cls) == c[(cname, "size")], cname
+        for f in structs[cname]:
+            assert getattr(cls, f).offset == c[(cname, f)], (cname, f)

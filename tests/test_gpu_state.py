@@ -148,3 +148,21 @@ def test_set_initial_matches_oracle(F):
     # the initial data matters: the default initial state gives another first step
     assert np.abs(mono[0]["lambda"] - ref0[0]["lambda"]).max() > 1e-6 * np.abs(ref0[0]["lambda"]).max()
     sol.close()
+
+
+def test_step_moves_only_scalars_across_the_host_link(F):
+    """fp_step reports its own host<->device copies: the per-step scalars and loop flags in,
+    flags, scalars and the status word out -- bytes, not vectors -- on the graph and the
+    stream path."""
+    case = W.small_case(3, 4, 4, k=2, n_steps=2)
+    for graph in (1, 0):
+        sol = F.Solver(case)
+        sol.set_option("graph", graph)
+        sol.assemble()
+        sol.factor()
+        for _ in range(2):
+            st = sol.step()
+            assert 0 < st["h2d_bytes"] <= 1024, (graph, st)
+            assert 0 < st["d2h_bytes"] <= 64 * 1024, (graph, st)
+            assert st["h2d_bytes"] < 8 * sol.sizes.n_lambda
+        sol.close()
