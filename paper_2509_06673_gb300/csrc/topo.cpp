@@ -6,6 +6,7 @@
 // displacement dofs, then (at P1 vertices) xi and p.  The local 3-field matrices are
 // symmetric quasi-definite, so LDL^T needs no pivoting in any ordering.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -338,6 +339,8 @@ bool build_topology(const fp_mesh_desc *m, const fp_params *p, Topology &T, std:
     if (dir) continue;
     if (!add_rows(1, 0, kv.first.second, kv.first.first, ent, 0)) { err = "node shared by >4 subdomains"; return false; }
   }
+  // device indexing of multiplier arrays (up to 6 entries per row) stays in int
+  if (T.lam_sa.size() > (size_t)(INT_MAX / 8)) { err = "too many interface multipliers"; return false; }
   T.n_lambda = (int)T.lam_sa.size();
   T.n_lambda_p = T.n_lambda - nlu;
   // ---- per-subdomain boundary scatter lists ----
