@@ -50,14 +50,14 @@ def test_c_client_steps_match_oracle(client):
         pytest.skip("no CUDA device")
     from paper_2509_06673_gb300 import workloads as W
     from oracle.monolithic import Discretization, solve_monolithic
-    r = _run(client, 3, 4, 4, 2, 2, 0, 1e-12)
+    r = _run(client, 3, 4, 4, 2, 2, 0, 1e-13)
     assert r.returncode == 0, (r.returncode, r.stderr)
     lines = r.stdout.split("\n")
     k = next(i for i, ln in enumerate(lines) if ln.startswith("lambda "))
     n = int(lines[k].split()[1])
     lam = np.array([float(v) for v in lines[k + 1: k + 1 + n]])
     assert sum(ln.startswith("step ") for ln in lines[:k]) == 2
-    case = W.small_case(3, 4, 4, k=2, n_steps=2, tol=1e-12)
+    case = W.small_case(3, 4, 4, k=2, n_steps=2, tol=1e-13)
     ref = solve_monolithic(case, Discretization(case))[-1]["lambda"]
     assert lam.shape == ref.shape
     assert np.abs(lam - ref).max() / np.abs(ref).max() < 1e-10
