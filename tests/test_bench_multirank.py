@@ -1,5 +1,6 @@
-"""The N > 1 path of bench.py on CPU: world-size-2 gloo ranks, each timing its own replica;
-the job rate uses the slowest rank's time (MAX over ranks) and counts every rank's steps."""
+"""bench.py on CPU: the N > 1 path with world-size-2 gloo ranks, each timing its own replica
+(the job rate uses the slowest rank's time, MAX over ranks, and counts every rank's steps); the
+JSON line of the reference arm (the oracle on the host cores) and its rank-0-only rule."""
 import os
 import socket
 
@@ -63,3 +64,38 @@ def test_traffic_record_requires_same_source_and_shape(tmp_path, monkeypatch):
     (fake / "band.cu").write_text("// changed\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_of(rec["workload"], rec["precision"], rec["shape"]) is None
+
+
+def _bench(args, env_extra=None):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, capture_output=True,
+                          text=True, timeout=900, env=env, cwd=root)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` times the oracle on a bounded sample and prints one JSON line
+    with the contract's keys; the reference line reports no host<->device bytes."""
+    import json
+    r = _bench(["--impl", "reference", "--config", "config5", "--steps", "1", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "config5" in d["config"]["workload"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "3"], {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0 and not r.stdout.strip(), (r.returncode, r.stdout, r.stderr)
