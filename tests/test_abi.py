@@ -186,3 +186,17 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert ctypes.sizeof(cls) == c[(cname, "size")], cname
         for f in structs[cname]:
             assert getattr(cls, f).offset == c[(cname, f)], (cname, f)
+
+
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_header_compiles_alone_pedantic(tmp_path, lang):
+    """include/fetipe.h is self-contained and warning-free as strict C11 and as C++17."""
+    import shutil
+    import subprocess
+    cc, std = ("gcc", "-std=c11") if lang == "c" else ("g++", "-std=c++17")
+    if shutil.which(cc) is None:
+        pytest.skip("no " + cc)
+    src = tmp_path / ("h.c" if lang == "c" else "h.cpp")
+    src.write_text('#include "fetipe.h"\nint main(void) { fp_sizes s; (void)s; return 0; }\n')
+    subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-c", str(src), "-o", str(tmp_path / "h.o")], check=True)
