@@ -6,9 +6,12 @@
 // displacement dofs, then (at P1 vertices) xi and p.  The local 3-field matrices are
 // symmetric quasi-definite, so LDL^T needs no pivoting in any ordering.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
+#include <exception>
 #include <map>
+#include <thread>
 #include <tuple>
 
 #include "internal.h"
@@ -207,6 +210,38 @@ void build_template(Template &t) {
   }
 }
 
+// Builds every template; templates are independent, so they are built by a small pool of
+// host threads pulling indices from a shared counter (an uneven partition has one template
+// per distinct subdomain shape, about a thousand for a 32 x 32 partition).  The result does
+// not depend on the number of threads.  An exception in a worker is rethrown here.
+void build_templates(std::vector<Template> &tpl) {
+  const int nt = (int)tpl.size();
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int nth = std::max(1, std::min(std::min(nt, 32), hw > 0 ? hw : 1));
+  std::atomic<int> next(0);
+  std::vector<std::exception_ptr> errs(nth);
+  auto work = [&](int w) {
+    try {
+      for (int i = next.fetch_add(1); i < nt; i = next.fetch_add(1)) build_template(tpl[i]);
+    } catch (...) {
+      errs[w] = std::current_exception();
+      next.store(nt);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < nth; ++w) {
+    try {
+      pool.emplace_back(work, w);
+    } catch (...) {
+      break;  // fewer threads: the remaining indices are taken by the others
+    }
+  }
+  work(0);
+  for (auto &th : pool) th.join();
+  for (auto &e : errs)
+    if (e) std::rethrow_exception(e);
+}
+
 struct NodeEnt { int s, d0, d1; };
 
 }  // namespace
@@ -250,11 +285,10 @@ bool build_topology(const fp_mesh_desc *m, const fp_params *p, Topology &T, std:
     auto it = tpl_index.find(key);
     int ti;
     if (it == tpl_index.end()) {
-      Template t;
+      Template t;  // numbered in first-use order; built below
       t.nx = nx; t.ny = ny; t.k = k; t.poro = poro;
       std::memcpy(t.side_u, su, sizeof su);
       std::memcpy(t.side_p, sp, sizeof sp);
-      build_template(t);
       ti = (int)T.tpl.size();
       T.tpl.push_back(std::move(t));
       tpl_index[key] = ti;
@@ -269,6 +303,7 @@ bool build_topology(const fp_mesh_desc *m, const fp_params *p, Topology &T, std:
     T.sub_I0[s] = k * cxs[cx]; T.sub_J0[s] = k * cys[cy];
     T.sub_i0[s] = cxs[cx]; T.sub_j0[s] = cys[cy];
   }
+  build_templates(T.tpl);
   // offsets
   T.vec_off.assign(S + 1, 0); T.fac_off.assign(S + 1, 0); T.csr_off.assign(S + 1, 0);
   T.unode_off.assign(S + 1, 0); T.pnode_off.assign(S + 1, 0); T.elem_off.assign(S + 1, 0);
