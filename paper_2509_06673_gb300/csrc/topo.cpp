@@ -139,24 +139,35 @@ void build_template(Template &t) {
   }
   t.b = bmax;
   t.LD = round_up(bmax + 1, 32);
-  // CSR pattern
-  std::vector<std::vector<int>> rows(n);
+  // CSR pattern: every (row, column) pair of every element, counted, filled, then sorted
+  // and made unique per row
+  std::vector<int> cnt(n + 1, 0);
+  for (int e = 0; e < ne; ++e) {
+    const int *ed = &t.elem_dofs[(size_t)e * t.ndl];
+    int valid = 0;
+    for (int c = 0; c < t.ndl; ++c) valid += ed[c] >= 0;
+    for (int a = 0; a < t.ndl; ++a)
+      if (ed[a] >= 0) cnt[ed[a] + 1] += valid;
+  }
+  for (int r = 0; r < n; ++r) cnt[r + 1] += cnt[r];
+  std::vector<int> all(cnt[n]), fill(cnt.begin(), cnt.end() - 1);
   for (int e = 0; e < ne; ++e) {
     const int *ed = &t.elem_dofs[(size_t)e * t.ndl];
     for (int a = 0; a < t.ndl; ++a) {
       if (ed[a] < 0) continue;
       for (int c = 0; c < t.ndl; ++c)
-        if (ed[c] >= 0) rows[ed[a]].push_back(ed[c]);
+        if (ed[c] >= 0) all[fill[ed[a]]++] = ed[c];
     }
   }
   t.csr_ptr.assign(n + 1, 0);
   t.csr_col.clear();
+  t.csr_col.reserve(cnt[n]);
   for (int r = 0; r < n; ++r) {
-    auto &v = rows[r];
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-    t.csr_ptr[r + 1] = t.csr_ptr[r] + (int)v.size();
-    t.csr_col.insert(t.csr_col.end(), v.begin(), v.end());
+    int *b0 = all.data() + cnt[r], *b1 = all.data() + cnt[r + 1];
+    std::sort(b0, b1);
+    b1 = std::unique(b0, b1);
+    t.csr_ptr[r + 1] = t.csr_ptr[r] + (int)(b1 - b0);
+    t.csr_col.insert(t.csr_col.end(), b0, b1);
   }
   // halo rows for the Dirichlet preconditioner
   t.halo_ptr.assign(1, 0);
@@ -186,26 +197,45 @@ void build_template(Template &t) {
   t.sell_col.clear();
   t.sell_src.clear();
   for (int q = 0; q < nslice; ++q) {
-    std::vector<std::vector<std::pair<int, int>>> ent(32);  // (col, src) per row of the slice
-    int w = 0;
+    // entries of row 32 q + l: (col, CSR index) of its non-fixed columns, or (r, -2) on a
+    // fixed row; slot k of the row at base + 32 k + l, padding (min(r, n - 1), -1)
+    int len[32], w = 0;
     for (int l = 0; l < 32; ++l) {
       const int r = 32 * q + l;
+      len[l] = 0;
       if (r >= n) continue;
       if (is_fixed(r)) {
-        ent[l].push_back({r, -2});
+        len[l] = 1;
       } else {
-        for (int e = t.csr_ptr[r]; e < t.csr_ptr[r + 1]; ++e)
-          if (!is_fixed(t.csr_col[e])) ent[l].push_back({t.csr_col[e], e});
+        for (int e = t.csr_ptr[r]; e < t.csr_ptr[r + 1]; ++e) len[l] += !is_fixed(t.csr_col[e]);
       }
-      w = std::max(w, (int)ent[l].size());
+      w = std::max(w, len[l]);
     }
-    for (int k2 = 0; k2 < w; ++k2)
-      for (int l = 0; l < 32; ++l) {
-        const int r = std::min(32 * q + l, n - 1);
-        const bool real = k2 < (int)ent[l].size();
-        t.sell_col.push_back(real ? ent[l][k2].first : r);
-        t.sell_src.push_back(real ? ent[l][k2].second : -1);
+    const size_t base = t.sell_col.size();
+    t.sell_col.resize(base + (size_t)32 * w);
+    t.sell_src.resize(base + (size_t)32 * w);
+    for (int l = 0; l < 32; ++l) {
+      const int r = 32 * q + l;
+      int k2 = 0;
+      if (r < n) {
+        if (is_fixed(r)) {
+          t.sell_col[base + l] = r;
+          t.sell_src[base + l] = -2;
+          k2 = 1;
+        } else {
+          for (int e = t.csr_ptr[r]; e < t.csr_ptr[r + 1]; ++e) {
+            if (is_fixed(t.csr_col[e])) continue;
+            t.sell_col[base + (size_t)32 * k2 + l] = t.csr_col[e];
+            t.sell_src[base + (size_t)32 * k2 + l] = e;
+            ++k2;
+          }
+        }
       }
+      for (; k2 < w; ++k2) {
+        t.sell_col[base + (size_t)32 * k2 + l] = std::min(r, n - 1);
+        t.sell_src[base + (size_t)32 * k2 + l] = -1;
+      }
+    }
     t.sell_ptr[q + 1] = (int)t.sell_col.size();
   }
 }
