@@ -18,10 +18,11 @@ def client(tmp_path_factory):
     from paper_2509_06673_gb300 import build
     lib = build.build()
     libdir = os.path.dirname(lib)
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(build.NVCC)), "lib64")   # libcudart of the toolkit
     exe = str(tmp_path_factory.mktemp("cclient") / "abi_steps")
     subprocess.run(["gcc", "-std=c11", "-O1", "-Wall", "-I", os.path.join(ROOT, "include"),
                     os.path.join(ROOT, "tests", "c", "abi_steps.c"), "-o", exe, "-L", libdir, "-lfetipe",
-                    "-Wl,-rpath," + libdir], check=True)
+                    "-L", cudalib, "-lcudart", "-Wl,-rpath," + libdir, "-Wl,-rpath," + cudalib], check=True)
     return exe
 
 
