@@ -179,6 +179,7 @@ fp_status fp_set_initial(fp_handle *h, const double *u0, const double *p0);
  * step that does not return FP_OK and returns its status.  FP_ERR_INVALID for n_steps < 0. */
 fp_status fp_run(fp_handle *h, int n_steps, fp_step_stats *last);
 
+/* Sizes of the handle's problem (host struct), valid from fp_create on. */
 fp_status fp_get_sizes(const fp_handle *h, fp_sizes *out);
 
 /* Host-only planning: validates mesh and params as fp_create does, builds the dof numbering
@@ -271,17 +272,35 @@ fp_status fp_get_step_timing(const fp_handle *h, double *ms4);
  * by the result.  Parameters: one flat FP32 array of
  * 68353 values: W1 [8 x 256] row-major, b1 [256], W2 [256 x 256] row-major, b2 [256],
  * W3 [256], b3 [1]. */
+/* Recording of training samples: with on = 1, every later fp_step with two earlier steps of
+ * history stores per_step (features, target) pairs, multipliers taken at an even stride, in a
+ * device store of max_samples pairs (grown, keeping what it holds, when max_samples exceeds
+ * its capacity; FP_ERR_OOM if it cannot be); the target is what the extrapolation misses,
+ * (lambda^n - lambda^{n-1} - rho dl) / s, the network's output units.  Recording stops silently when the store is full.  on = 0 stops it.
+ * FP_ERR_INVALID for max_samples < 0 or per_step < 1. */
 fp_status fp_learned_record(fp_handle *h, int on, long long max_samples, int per_step);
+/* Use (on = 1) or not the learned guess in fp_step; FP_ERR_STATE while the network has no
+ * parameters (fp_mlp_init, fp_mlp_set_params or fp_learned_train first). */
 fp_status fp_learned_use(fp_handle *h, int on);
+/* Trains the network on the recorded samples with Adam (learning rate lr), `epochs` passes
+ * of minibatches of `batch` samples (32 <= batch <= 65536) in a SplitMix64 shuffle from
+ * `seed`; initialises the parameters (fp_mlp_init(seed)) if there are none.  last_loss
+ * (may be NULL): the mean loss of the last epoch.  FP_ERR_STATE with fewer samples than one
+ * batch; FP_ERR_INVALID for epochs < 1 or lr <= 0. */
 fp_status fp_learned_train(fp_handle *h, int epochs, int batch, double lr, unsigned long long seed,
                            double *last_loss);
+/* Number of recorded samples. */
 fp_status fp_learned_num_samples(const fp_handle *h, long long *n);
 /* He-uniform W1, W2 from SplitMix64 stream `seed` (value i -> parameter i); W3 and biases 0. */
 fp_status fp_mlp_init(fp_handle *h, unsigned long long seed);
+/* Copy the flat parameter array in (set) or out (get); n must be 68353 (FP_ERR_INVALID
+ * otherwise); get returns FP_ERR_STATE while there are no parameters. */
 fp_status fp_mlp_set_params(fp_handle *h, const float *host, int n);
 fp_status fp_mlp_get_params(const fp_handle *h, float *host, int n);
-/* Forward pass / mean-squared-error loss L = sum((out - y)^2) / (2 rows) and its gradient,
- * on host arrays of at most 65536 rows (x: rows x 8). */
+/* Forward pass / mean-squared-error loss L = sum((out - y)^2) / (2 rows) and its gradient
+ * (68353 floats in the parameter layout), on host arrays of 1 to 65536 rows (x: rows x 8,
+ * row-major); FP_ERR_STATE while the network has no parameters.  For checking the kernels
+ * against a reference; training uses the same kernels on device-resident samples. */
 fp_status fp_mlp_forward(fp_handle *h, const float *x, int rows, float *out);
 fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int rows, float *grad,
                            double *loss);
