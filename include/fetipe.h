@@ -398,7 +398,12 @@ typedef struct {
 } fp_tuning;
 fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out);
 
+/* Message of the last failed call on h; with h = NULL, of the last failed fp_create or
+ * fp_plan on the calling thread.  The string is owned by the library and valid until the
+ * next call on h (or on the thread). */
 const char *fp_last_error(const fp_handle *h);
+/* Frees everything the handle owns (device memory, streams, events, graphs); NULL is a no-op.
+ * The handle's stream must be idle. */
 void fp_destroy(fp_handle *h);
 
 #ifdef __cplusplus
