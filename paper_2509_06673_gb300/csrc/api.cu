@@ -246,6 +246,14 @@ fp_status dalloc(fp_handle *h, V **ptr, size_t count) {
   return FP_OK;
 }
 
+// Frees one allocation made by dalloc (cudaFree waits for the device to finish with it).
+void dfree(fp_handle *h, void *p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) h->allocs.erase(it);
+  cudaFree(p);
+}
+
 template <typename V>
 fp_status upload(fp_handle *h, const V **dst, const std::vector<V> &src) {
   V *p = nullptr;
@@ -2000,6 +2008,9 @@ fp_status fp_learned_record(fp_handle *h, int on, long long max_samples, int per
       CK(cudaMemcpyAsync(sx, h->SX, h->n_samples * MLP_NIN * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     if (h->SY && h->n_samples)
       CK(cudaMemcpyAsync(sy, h->SY, h->n_samples * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h, h->SX);  // the smaller store it replaces
+    dfree(h, h->SY);
     h->SX = sx; h->SY = sy; h->cap_samples = max_samples;
   }
   h->learned_record = on ? 1 : 0;
