@@ -200,3 +200,14 @@ def test_header_compiles_alone_pedantic(tmp_path, lang):
     src.write_text('#include "fetipe.h"\nint main(void) { fp_sizes s; (void)s; return 0; }\n')
     subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
                     "-c", str(src), "-o", str(tmp_path / "h.o")], check=True)
+
+
+def test_every_option_key_is_documented():
+    """The keys fp_set_option accepts (csrc/api.cu) are exactly the keys the header documents."""
+    api = open(os.path.join(ROOT, "paper_2509_06673_gb300", "csrc", "api.cu")).read()
+    i = api.index("fp_status fp_set_option(fp_handle *h, const char *key, double value) {")
+    accepted = set(re.findall(r'k == "(\w+)"', api[i: api.index("\n}\n", i)]))
+    hdr = open(os.path.join(ROOT, "include", "fetipe.h")).read()
+    doc = hdr[hdr.index("Tunables of the solve"): hdr.index("fp_status fp_set_option")]
+    documented = set(re.findall(r'^\s*\*\s+"(\w+)"\s*\[', doc, flags=re.M))
+    assert accepted and accepted == documented, accepted ^ documented
