@@ -123,6 +123,7 @@ _lib.fp_mlp_loss_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.POINT
 _lib.fp_last_error.argtypes = [_vp]
 _lib.fp_last_error.restype = ctypes.c_char_p
 _lib.fp_destroy.argtypes = [_vp]
+_lib.fp_destroy.restype = None
 
 
 class FetipeError(RuntimeError):

@@ -211,3 +211,23 @@ def test_every_option_key_is_documented():
     doc = hdr[hdr.index("Tunables of the solve"): hdr.index("fp_status fp_set_option")]
     documented = set(re.findall(r'^\s*\*\s+"(\w+)"\s*\[', doc, flags=re.M))
     assert accepted and accepted == documented, accepted ^ documented
+
+
+def test_binding_argtypes_match_the_header():
+    """Every ctypes prototype of the binding has the header's parameter count, a pointer where
+    the header has a pointer and the same scalar type where it has a scalar."""
+    from paper_2509_06673_gb300 import fetipe
+    ptr_like = (ctypes.c_void_p, ctypes.c_char_p)
+    for name, (ret, args) in _signatures().items():
+        fn = getattr(fetipe._lib, name)
+        bound = fn.argtypes
+        assert bound is not None and len(bound) == len(args), name
+        for i, (want, got) in enumerate(zip(args, bound)):
+            if want is ctypes.c_void_p:
+                assert got in ptr_like or issubclass(got, ctypes._Pointer), (name, i, got)
+            else:
+                assert got is want, (name, i, got, want)
+        if ret == "void":
+            assert fn.restype is None, name
+        elif ret == "fp_status":
+            assert fn.restype is ctypes.c_int, name
