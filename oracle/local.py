@@ -14,8 +14,11 @@ Dirichlet values of u (and of p) are eliminated by lifting.  Readings: W_h = M_h
 (Sec. 2.4), so xi and eta carry every P1 node and only p carries the pressure Dirichlet
 condition; the elastic load is f_E (the "f_P" in Eq. (2.38) is a misprint).
 
-Pinned by tests/test_oracle_local.py and, through the whole solve, by the convergence and
-transmission tests.
+Pinned by the convergence-order, patch, eta-reduction and transmission tests
+(tests/test_oracle_solution.py, tests/test_oracle_problem.py), the initial-data test
+(tests/test_oracle_initial.py), the point-source load and fluid-balance tests
+(tests/test_oracle_point_source.py), the dense 3-field comparison and the block-system
+residual (tests/test_oracle_feti.py).
 """
 import numpy as np
 import scipy.sparse as sp
