@@ -128,6 +128,10 @@ typedef struct {
   long long h2d_bytes;       /* host -> device bytes the step copied (per-step scalars, loop flags) */
   long long d2h_bytes;       /* device -> host bytes the step copied (loop flags, scalars, status);
                                 the caller's fp_get_* reads are not included */
+  long long kernel_launches; /* kernels of the library this step launched ("graph" 1: the kernel
+                                nodes of the step graph, of its outer loop body per round and of
+                                its inner loop body per execution, counted on the device, plus the
+                                sample-recording kernels; -1 with "graph" 0, not counted) */
 } fp_step_stats;
 
 /* Copies the mesh description and parameters, builds the dof numbering, band ordering and
@@ -233,16 +237,20 @@ fp_status fp_apply_precond(fp_handle *h, const double *v, double *out, int on_de
 fp_status fp_apply_projection(fp_handle *h, const double *v, double *out, int on_device);
 
 /* Same result as fp_apply_projection, for callers that cannot allocate device memory at
- * call time (for instance while a CUDA stream is being captured into a graph, or inside a
- * runtime that owns every allocation).  The paper has no counterpart: this is a library
- * convenience.  v and out are device pointers of the handle's device (n_lambda doubles;
- * they may alias).  The call allocates nothing: its scratch (two vectors of 3 * n_floating
- * doubles) is a fixed array of 2 * 24576 doubles (384 KiB) compiled into the library and
- * kept on every device that loads it until the process exits; more than 8192 floating
- * subdomains is rejected with FP_ERR_INVALID.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress), so make it before any stream capture.
- * Every call shares the array: calls that overlap on the GPU (other streams, other
- * threads, other handles on the same device) race; serialise them.  Synchronous. */
+ * call time: an application that reserves the device's memory for its own pool up front (so
+ * a library cudaMalloc fails or breaks its budget), or a latency-bound loop that may not take
+ * cudaMalloc's implicit device synchronisation.  The paper has no counterpart: this is a
+ * library convenience.  v and out are device pointers of the handle's device (n_lambda
+ * doubles; they may alias).  The call allocates nothing: its scratch (two vectors of
+ * 3 * n_floating doubles) is a fixed array of 2 * 24576 doubles (384 KiB) compiled into the
+ * library and kept on every device that loads it until the process exits; a problem with
+ * more than 8192 floating subdomains is rejected with FP_ERR_INVALID (checked first, right
+ * after fp_create).  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make that first call
+ * before any stream capture, and do not use the library across cudaDeviceReset.  Every call
+ * shares the array and leaves its last contents there: calls that overlap on the GPU (other
+ * streams, other threads, other handles on the same device) race; serialise them.  The call
+ * waits for its kernels (it synchronises the handle's stream) and reports their errors. */
 fp_status fp_apply_projection_noalloc(fp_handle *h, const double *v, double *out);
 
 /* Local dof map of subdomain s (host, n_s ints each): field (0 u_x, 1 u_y, 2 xi, 3 p) and
@@ -360,6 +368,24 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *   "stag_window"  [60] a round of Algorithm 1 stops (and restarts from the true residual)
  *                       when its recursive residual has not halved within this many
  *                       iterations; 0 never, 1..100000
+ *   "factor_tc"    [1]  FP32 factorisations run on the tensor cores: right-looking panels of 32
+ *                       columns, the dense trailing updates as tcgen05 TF32 tiles with the
+ *                       3xTF32 split (hi*hi + hi*lo + lo*hi, about FP32 accuracy); half
+ *                       bandwidth <= 511.  Mixed precision with "factor_fp64": the Dirichlet
+ *                       factor (preconditioner only) this way, the Neumann factor in FP64;
+ *                       without "factor_fp64": both.  0: CUDA-core factorisation
+ *   "explicit_2f"  [1]  mixed precision with "explicit" and "factor_fp64": the accurate F applies
+ *                       (reference, initial, learned-guess and true residuals) multiply by F_s
+ *                       stored as FP32 hi/lo pairs of its upper 32 x 32 tiles (FP32 arithmetic
+ *                       with error-free products and sums, ~1e-14 relative) instead of the FP64
+ *                       F_s; 0: the FP64 F_s
+ *   "coarse_2f"    [1]  mixed precision: the coarse projection multiplies by (G^T G)^{-1} stored
+ *                       as FP32 hi/lo pairs of its upper 32 x 32 tiles (half the bytes, FP32
+ *                       arithmetic with error-free products and sums, ~1e-14 relative); 0: the
+ *                       dense FP64 product.  The tiles are packed at fp_factor; the FP64 path
+ *                       always uses the FP64 product
+ *   "tol"          [fp_params.tol] relative projected residual at which Algorithm 1 stops,
+ *                       0 < tol < 1; takes effect at the next fp_step
  */
 fp_status fp_set_option(fp_handle *h, const char *key, double value);
 
@@ -395,6 +421,17 @@ typedef struct {
    * residual norm per iteration over 30 iterations of Algorithm 1 on a seeded random
    * right-hand side in range(P) from lambda_0 = 0, and the time per iteration */
   double precond_rate[2], precond_ms_per_it[2];
+  /* kernel instantiations in use after the last fp_factor.  solve_mmax: the band-solve
+   * template's window registers per lane (LD / 32 of the widest band, rounded up to 4, 8, 12
+   * or 16).  Per explicit operator (index 0 F_s, 1 S_s; zero when not built): the
+   * multi-right-hand-side build's rows per thread of the off-block coupling (mrhs_nr: 4, 8,
+   * 12 or 16), right-hand sides per tile (mrhs_mt: 32, or 16 where a 32-wide window does
+   * not fit in shared memory) and element size in bytes (mrhs_esz: 8 FP64, 4 FP32). */
+  int solve_mmax;
+  int mrhs_nr[2], mrhs_mt[2], mrhs_esz[2];
+  /* device time of the FP32 factorisations on the tensor cores ("factor_tc"; index 0 Neumann,
+   * 1 Dirichlet), milliseconds; 0 where that factor was not computed this way */
+  double factor_tc_ms[2];
 } fp_tuning;
 fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out);
 

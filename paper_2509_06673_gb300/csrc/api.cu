@@ -37,12 +37,21 @@ cudaError_t launch_band_mrhs(bool fp32, int bmax, int mt, int grid, cudaStream_t
                              const long long *linv_off, const double *csr, int kind, void *scratch, long long sstride,
                              int *counter, void *out, const long long *out_off, int R, int LDp);
 int mrhs_blocks_per_sm(bool fp32, int bmax, int mt, int R, int LDp);
+int mrhs_nr(int b, int mt);
 cudaError_t launch_explicit_apply(bool fp32, DevTopo D, int S, int mmax_bnd, const void *ops, const long long *op_off,
                                   double *xloc, const int *fl, cudaStream_t st);
+cudaError_t launch_pack_sym2f(DevTopo D, int S, const double *full, const long long *full_off, float *tiles,
+                              const long long *tile_off, cudaStream_t st);
+cudaError_t launch_explicit_apply_sym2f(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
+                                        double *xloc, const int *fl, cudaStream_t st);
 cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, const long long *full_off,
                             float *tiles, const long long *tile_off, cudaStream_t st);
 cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
-                                      double *xloc, const int *fl, cudaStream_t st);
+                                      double *xloc, const int *fl, cudaStream_t st, const double *vlam,
+                                      int skip_fixed);
+__global__ void k_gather_wscale(DevTopo, const double *, double *, const int *);
+__global__ void k_Gcomb_dot(DevTopo, const double *, const double *, double *, const double *, double *, unsigned *,
+                            double *, int *, int);
 __global__ void k_dot(const double *, const double *, long long, double *, unsigned *, double *, int *, int,
                       double *, int);
 __global__ void k_pcg_update(double *, double *, const double *, const double *, long long, double *, unsigned *,
@@ -54,8 +63,15 @@ __global__ void k_gather(DevTopo, const double *, double *, const int *);
 __global__ void k_wscale(DevTopo, const double *, double *, const int *);
 __global__ void k_halo(DevTopo, const double *, const double *, double *, const int *);
 __global__ void k_bnd_apply(DevTopo, const double *, const double *, double *, const int *);
-__global__ void k_Gt(DevTopo, const double *, double *, const int *);
+__global__ void k_Gt(DevTopo, const double *, double *, const int *, float *);
+__global__ void k_pack_float_g(DevTopo, double *);
 cudaError_t launch_gemv(const double *H, const double *y, double *alpha, int nH, const int *fl, cudaStream_t st);
+cudaError_t launch_coarse_pack2f(const double *H, int nH, float *tiles, cudaStream_t st);
+size_t band_factor_tc_smem(int ldmax, int bmax);
+cudaError_t launch_band_factor_tc(const BandTask *tasks, int ntask, float *base, int ldmax, int bmax, int num_sms,
+                                  int *counter, int *status, cudaStream_t stream);
+cudaError_t launch_coarse_apply2f(const float *tiles, int nH, const float *ysplit, double *part, double *alpha,
+                                  const int *fl, cudaStream_t st);
 __global__ void k_Gcomb(DevTopo, const double *, const double *, double, double *, const int *);
 __global__ void k_rhs(DevTopo, DevParams, const double *, const double *, const double *, const double *,
                       const double *, double *, double *);
@@ -139,13 +155,21 @@ struct fp_handle {
   // the PCG loop's operators: FP64 full m x mp matrices (FP64), FP32 upper 32 x 32 tiles (mixed)
   void *opF = nullptr, *opS = nullptr;
   double *opF64 = nullptr;              // mixed precision: F_s in FP64 for the accurate applies
+  float *opF2 = nullptr;                // ... and as two-float (hi/lo FP32) symmetric tiles
+  int explicit_2f = 1;                  // option: accurate mixed-precision F applies from opF2
   const long long *op_off = nullptr, *tile_off = nullptr, *linv_off_dev = nullptr;
   long long op_total = 0, tile_total = 0;
   const int *mrhs_s[2] = {}, *mrhs_j0[2] = {};  // build tasks for tiles of 32 / 16 right-hand sides
   int mrhs_ntask[2] = {0, 0};
   double explicit_build_ms = 0;
   int factor_fp64 = 1;     // mixed precision: factor in FP64, round the finished factor to FP32
+  int factor_tc = 1;       // FP32 factors on the tensor cores (3xTF32 trailing updates)
   double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
+  // mixed precision: (G^T G)^{-1} as hi/lo FP32 upper tiles and the apply's FP64 partials
+  float *Htiles = nullptr, *cysplit = nullptr;
+  double *Hpart = nullptr;
+  int coarse_2f = 1;       // option: two-float tiled coarse product in mixed precision
+  int gkernels[3] = {0, 0, 0};  // kernel nodes of the step graph: top level, outer body, inner body
   BandTask *tasksN = nullptr, *tasksD = nullptr, *taskH = nullptr, *tasksHinv = nullptr;
   int ntask = 0, mmax = 4, mmaxH = 4, ldmax = 32;
   int *counter = nullptr, *status = nullptr;
@@ -331,6 +355,11 @@ fp_status build_device(fp_handle *h) {
   TRY(dalloc(h, &h->ga, 3 * (size_t)T.n_lambda));
   TRY(dalloc(h, &h->gb, 3 * (size_t)T.n_lambda));
   D.lam_ga = h->ga; D.lam_gb = h->gb;
+  {
+    double *fg = nullptr;
+    TRY(dalloc(h, &fg, 3 * std::max<size_t>(T.float_rows.size(), 1)));
+    D.float_g = fg;
+  }
   // params
   DevParams &P = h->DP;
   P.lam = h->P.lame_lambda; P.mu = h->P.mu; P.alpha = h->P.alpha; P.c0 = h->P.c0;
@@ -629,10 +658,33 @@ fp_status apply_P(fp_handle *h, const double *v, double *out, const int *fl) {
     if (out != v) CK(cudaMemcpyAsync(out, v, nl * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     return FP_OK;
   }
-  k_Gt<<<(h->T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->cy, fl);
+  const bool two_float = h->Htiles && h->coarse_2f;
+  k_Gt<<<(h->T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->cy, fl, two_float ? h->cysplit : nullptr);
   CKL();
-  CK(launch_gemv(h->Hinv, h->cy, h->calpha, h->T.nH, fl, h->stream));
+  if (two_float) CK(launch_coarse_apply2f(h->Htiles, h->T.nH, h->cysplit, h->Hpart, h->calpha, fl, h->stream));
+  else CK(launch_gemv(h->Hinv, h->cy, h->calpha, h->T.nH, fl, h->stream));
   k_Gcomb<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->calpha, v, -1.0, out, fl);
+  CKL();
+  return FP_OK;
+}
+
+fp_status dot(fp_handle *h, const double *a, const double *b, int op, double *slot, const int *check);
+
+// out = P v, then dot(a, out) -> op (Algorithm 1's reductions after a projection; the last
+// projection kernel and the reduction are one launch when there is a coarse space)
+fp_status apply_P_dot(fp_handle *h, const double *v, double *out, const double *a, int op) {
+  const int nl = h->T.n_lambda;
+  if (!h->T.NF) {
+    if (out != v) CK(cudaMemcpyAsync(out, v, nl * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return dot(h, a, out, op, nullptr, h->fl);
+  }
+  const bool two_float = h->Htiles && h->coarse_2f;
+  k_Gt<<<(h->T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->cy, h->fl, two_float ? h->cysplit : nullptr);
+  CKL();
+  if (two_float) CK(launch_coarse_apply2f(h->Htiles, h->T.nH, h->cysplit, h->Hpart, h->calpha, h->fl, h->stream));
+  else CK(launch_gemv(h->Hinv, h->cy, h->calpha, h->T.nH, h->fl, h->stream));
+  k_Gcomb_dot<<<RED_BLOCKS, 256, 0, h->stream>>>(h->D, h->calpha, v, out, a, h->partial, h->red_counter, h->sc,
+                                                 h->fl, op);
   CKL();
   return FP_OK;
 }
@@ -647,11 +699,17 @@ fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, boo
   const bool mixed = h->P.precision == FP_PREC_MIXED;
   const void *op = nullptr;
   if (h->ops_ready) op = !mixed || !accurate ? h->opF : (h->opF64_ready ? h->opF64 : nullptr);
-  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, v, 1.0, h->XB, 1, fl, op ? 0 : 1);
-  CKL();
+  const bool fused = op && mixed && !accurate;  // the tiled FP32 apply forms B^T v itself
+  if (!fused) {
+    k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, v, 1.0, h->XB, 1, fl, op ? 0 : 1);
+    CKL();
+  }
   if (op) {
-    if (mixed && !accurate)
-      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)op, h->tile_off, h->XB, fl, h->stream));
+    if (fused)
+      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)op, h->tile_off, h->XB, fl, h->stream,
+                                   v, 1));
+    else if (mixed && h->opF2 && h->explicit_2f)
+      CK(launch_explicit_apply_sym2f(h->D, h->T.S, h->nbnd_max, h->opF2, h->tile_off, h->XB, fl, h->stream));
     else
       CK(launch_explicit_apply(false, h->D, h->T.S, h->nbnd_max, op, h->op_off, h->XB, fl, h->stream));
     k_gather<<<(h->T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->XB, out, fl);
@@ -682,14 +740,18 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
   }
   if (h->P.precond == FP_PRECOND_LUMPED) return apply_M_lumped(h, v, out, fl);
   k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
-  k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl, h->ops_ready ? 0 : 1);
+  const bool fused = h->ops_ready && h->P.precision == FP_PREC_MIXED;  // tiled apply forms B^T W v itself
+  if (!fused) k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl, h->ops_ready ? 0 : 1);
   CKL();
   if (h->ops_ready) {
-    if (h->P.precision == FP_PREC_MIXED)
+    if (fused) {
       CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)h->opS, h->tile_off, h->XP, fl,
-                                   h->stream));
-    else
-      CK(launch_explicit_apply(false, h->D, h->T.S, h->nbnd_max, h->opS, h->op_off, h->XP, fl, h->stream));
+                                   h->stream, h->t1, 0));
+      k_gather_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, out, fl);
+      CKL();
+      return FP_OK;
+    }
+    CK(launch_explicit_apply(false, h->D, h->T.S, h->nbnd_max, h->opS, h->op_off, h->XP, fl, h->stream));
   } else {
     k_halo<<<h->T.S, 256, 0, h->stream>>>(h->D, h->csr_val, h->XP, h->XY, fl);
     CKL();
@@ -808,6 +870,31 @@ fp_status choose_nb(fp_handle *h, bool dbl, const BandTask *tasks, void *buf, in
 fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, int kind, void *out);
 fp_status alloc_op(fp_handle *h, void **p, size_t bytes);
 
+// FP32 factorisation on the tensor cores (k_band_factor_tc): usable when the widest band's
+// operands fit in shared memory (half bandwidth <= 511)
+bool tc_ok(const fp_handle *h) {
+  int bmax = 0;
+  for (const Template &t : h->T.tpl) bmax = std::max(bmax, t.b);
+  return h->factor_tc && bmax <= 511 && band_factor_tc_smem(h->ldmax, bmax) <= 227 * 1024;
+}
+
+// band of K_s (mode 0 Neumann, 1 Dirichlet) in FP32, factorised with 3xTF32 tensor-core trailing
+// updates, then the inverse diagonal blocks of the solves; timed with events into factor_tc_ms
+fp_status factor_fp32_tc(fp_handle *h, const BandTask *tk, float *fac, float *linv, int mode) {
+  int bmax = 0;
+  for (const Template &t : h->T.tpl) bmax = std::max(bmax, t.b);
+  CK(launch_csr_to_band(true, h->D, h->csr_val, fac, mode, h->stream));
+  CK(cudaEventRecord(h->ev[4], h->stream));
+  CK(launch_band_factor_tc(tk, h->ntask, fac, h->ldmax, bmax, h->num_sms, h->counter, h->status, h->stream));
+  CK(cudaEventRecord(h->ev[5], h->stream));
+  CK(launch_band_linv(true, tk, h->ntask, fac, linv, h->stream));
+  CK(cudaEventSynchronize(h->ev[5]));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]);
+  h->tuning.factor_tc_ms[mode] = ms;
+  return FP_OK;
+}
+
 template <typename T>
 fp_status factor_T(fp_handle *h) {
   Topology &Tp = h->T;
@@ -838,6 +925,12 @@ fp_status factor_T(fp_handle *h) {
       T *dstF = (T *)(mode == 0 ? h->facN : h->facD);
       T *dstL = (T *)(mode == 0 ? h->linvN : h->linvD);
       const BandTask *tk = mode == 0 ? h->tasksN : h->tasksD;
+      if (mode == 1 && tc_ok(h)) {
+        // the Dirichlet factor serves only the preconditioner (S_s, or its band solves): FP32 on
+        // the tensor cores, no FP64 copy
+        st = factor_fp32_tc(h, tk, (float *)dstF, (float *)dstL, 1);
+        continue;
+      }
       cudaError_t ee = launch_csr_to_band(false, h->D, h->csr_val, tN, mode, h->stream);
       if (ee == cudaSuccess) ee = launch_band_factor(false, tk, h->ntask, tN, NB, h->status, smem, h->stream);
       if (ee == cudaSuccess) ee = launch_band_linv(false, tk, h->ntask, tN, tL, h->stream);
@@ -854,6 +947,11 @@ fp_status factor_T(fp_handle *h) {
           ee = launch_pack_sym(true, h->D, h->T.S, h->opF64, h->op_off, (float *)h->opF, h->tile_off, h->stream);
           if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
         }
+        if (st == FP_OK) st = alloc_op(h, (void **)&h->opF2, (size_t)h->tile_total * 8);
+        if (st == FP_OK) {
+          ee = launch_pack_sym2f(h->D, h->T.S, h->opF64, h->op_off, h->opF2, h->tile_off, h->stream);
+          if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
+        }
         if (st == FP_OK) h->opF64_ready = 1;
       }
     }
@@ -861,6 +959,11 @@ fp_status factor_T(fp_handle *h) {
     cudaFree(tN);
     cudaFree(tL);
     return st;
+  }
+  if (f32 && tc_ok(h)) {
+    TRY(factor_fp32_tc(h, h->tasksN, (float *)fN, (float *)h->linvN, 0));
+    TRY(factor_fp32_tc(h, h->tasksD, (float *)fD, (float *)h->linvD, 1));
+    return FP_OK;
   }
   int NB = 32;
   TRY(choose_nb(h, !f32, h->tasksN, fN, &NB));
@@ -884,6 +987,7 @@ fp_status factor_coarse(fp_handle *h) {
     TRY(dalloc(h, &h->linvH, 1024 * (size_t)((T.nH + 31) / 32)));
   }
   k_coarse_G<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->ga, h->gb);
+  k_pack_float_g<<<(T.NF + 7) / 8, 256, 0, h->stream>>>(h->D, const_cast<double *>(h->D.float_g));
   CK(cudaMemsetAsync(h->Hband, 0, (size_t)T.nH * T.LDH * sizeof(double), h->stream));
   k_coarse_GtG<<<(T.NF + 127) / 128, 128, 0, h->stream>>>(h->D, h->ga, h->gb, h->Hband);
   CKL();
@@ -895,6 +999,15 @@ fp_status factor_coarse(fp_handle *h) {
   CKL();
   CK(launch_band_linv(false, h->taskH, 1, h->Hband, h->linvH, h->stream));
   TRY(launch_solve(h, false, h->tasksHinv, T.nH, h->Hband, h->linvH, h->Hinv, h->mmaxH, nullptr));
+  if (h->P.precision == FP_PREC_MIXED && h->coarse_2f) {
+    const long long nt = (T.nH + 31) / 32, ntile = nt * (nt + 1) / 2;
+    if (!h->Htiles) {
+      TRY(dalloc(h, &h->Htiles, (size_t)ntile * 2048));
+      TRY(dalloc(h, &h->Hpart, (size_t)ntile * 64));   // two-float partials: 2 x ntile x 32 float pairs
+      TRY(dalloc(h, &h->cysplit, 2 * (size_t)T.nH));
+    }
+    CK(launch_coarse_pack2f(h->Hinv, T.nH, h->Htiles, h->stream));
+  }
   return FP_OK;
 }
 
@@ -1001,6 +1114,9 @@ fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, i
     return FP_ERR_INVALID;
   }
   const int grid = std::min(bps * h->num_sms, std::max(1, h->mrhs_ntask[w]));
+  h->tuning.mrhs_nr[kind] = mrhs_nr(bmax, mt);
+  h->tuning.mrhs_mt[kind] = mt;
+  h->tuning.mrhs_esz[kind] = (int)esz;
   CK(cudaMemsetAsync(out, 0, (size_t)h->op_total * esz, h->stream));
   const long long sstride = (long long)nmax * mt;
   void *scratch = nullptr;
@@ -1254,13 +1370,11 @@ fp_status pcg_iteration(fp_handle *h) {
   const int nl = h->T.n_lambda;
   cudaStream_t s = h->stream;
   TRY(apply_F(h, h->p, h->q, h->fl, false));
-  TRY(apply_P(h, h->q, h->q, h->fl));
-  TRY(dot(h, h->p, h->q, OP_PQ, nullptr, h->fl));
+  TRY(apply_P_dot(h, h->q, h->q, h->p, OP_PQ));
   k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
   CKL();
   TRY(apply_M(h, h->r, h->z, h->fl));
-  TRY(apply_P(h, h->z, h->z, h->fl));
-  TRY(dot(h, h->r, h->z, OP_RZ, nullptr, h->fl));
+  TRY(apply_P_dot(h, h->z, h->z, h->r, OP_RZ));
   k_pcg_pupdate<<<(nl + 255) / 256, 256, 0, s>>>(h->p, h->z, nl, h->sc, h->fl);
   CKL();
   return FP_OK;
@@ -1311,6 +1425,20 @@ fp_status krylov_stream(fp_handle *h, int *restarts_out) {
 // kernel that sets its first condition value, `body` records the body on capture stream
 // cap[depth] (the body's last kernel sets the condition for the next round).
 using CondFn = std::function<fp_status(cudaGraphConditionalHandle)>;
+// kernel nodes of a graph (not those of the bodies of its conditional nodes)
+int count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  int k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
 fp_status capture_while(fp_handle *h, int depth, const CondFn &arm, const CondFn &body) {
   cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
   cudaGraph_t cg = nullptr;
@@ -1346,6 +1474,7 @@ fp_status capture_while(fp_handle *h, int depth, const CondFn &arm, const CondFn
   const cudaError_t e = cudaStreamEndCapture(bs, &ended);
   if (st != FP_OK) return st;
   if (e != cudaSuccess) { h->err = std::string("capture of a loop body: ") + cudaGetErrorString(e); return FP_ERR_CUDA; }
+  h->gkernels[depth] = count_kernel_nodes(bodyg);
   CK(cudaStreamUpdateCaptureDependencies(outer, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
   return FP_OK;
 }
@@ -1390,7 +1519,7 @@ fp_status step_recovery(fp_handle *h) {
   cudaStream_t s = h->stream;
   if (T.NF) {
     TRY(lincomb(h, h->t1, h->t2, 1.0, h->d, -1.0, nullptr));
-    k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr);
+    k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, s>>>(h->D, h->t1, h->cy, nullptr, nullptr);
     CK(launch_gemv(h->Hinv, h->cy, h->calpha, T.nH, nullptr, s));
     CKL();
   }
@@ -1455,6 +1584,7 @@ fp_status capture_step(fp_handle *h, bool use_learned) {
     return FP_ERR_CUDA;
   }
   h->graph = g;
+  h->gkernels[0] = count_kernel_nodes(g);
   h->gkey = use_learned ? 1 : 0;
   h->gdirty = 0;
   return FP_OK;
@@ -1625,6 +1755,9 @@ fp_status fp_factor(fp_handle *h) {
   h->ops_ready = 0;
   h->opF64_ready = 0;
   h->tuning.explicit_ms = 0;
+  h->tuning.solve_mmax = h->mmax;
+  h->tuning.factor_tc_ms[0] = h->tuning.factor_tc_ms[1] = 0.0;
+  for (int k = 0; k < 2; ++k) h->tuning.mrhs_nr[k] = h->tuning.mrhs_mt[k] = h->tuning.mrhs_esz[k] = 0;
   CK(cudaMemsetAsync(h->ir_prev, 0, 2 * sizeof(double), h->stream));
   TRY(h->P.precision == FP_PREC_MIXED ? factor_T<float>(h) : factor_T<double>(h));
   TRY(factor_coarse(h));
@@ -1679,8 +1812,10 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
     TRY(step_recovery(h));
   }
   // training samples: features of this step and target (lambda^n - lambda^{n-1}) / s1
+  int extra_launches = 0;
   if (h->learned_record && h->hist >= 2 && h->n_samples < h->cap_samples) {
     if (!use_learned) TRY(build_features(h));
+    extra_launches = 1 + (use_learned ? 0 : 4);  // k_record, and build_features' four kernels
     const int per = std::min(h->record_per_step, nl);
     const int stride = std::max(1, nl / per);
     const int r0 = (int)(h->step_n % stride);
@@ -1734,6 +1869,11 @@ fp_status fp_step(fp_handle *h, fp_step_stats *stats) {
     stats->stagnations = h->h_fl[FL_NSTAG];
     stats->h2d_bytes = h->xfer[0];
     stats->d2h_bytes = h->xfer[1];
+    // graph path: the step graph's kernel nodes, the outer body's per round, the inner body's per
+    // execution (counted on the device), plus the recording kernels launched after the graph
+    stats->kernel_launches = h->use_graph ? h->gkernels[0] + (long long)(restarts + 1) * h->gkernels[1] +
+                                                (long long)h->h_fl[FL_NINNER] * h->gkernels[2] + extra_launches
+                                          : -1;
   }
   fp_status st = check_status(h);
   if (st) return st;
@@ -2153,6 +2293,10 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "explicit") { if (v < 0 || v > 1) return bad(); h->explicit_ops = v; }
   else if (k == "explicit_tile") { if (v != 0 && v != 16 && v != 32) return bad(); h->explicit_tile = v; }
   else if (k == "autotune") { if (v < 0 || v > 1) return bad(); h->autotune = v; }
+  else if (k == "factor_tc") { if (v < 0 || v > 1) return bad(); h->factor_tc = v; }
+  else if (k == "explicit_2f") { if (v < 0 || v > 1) return bad(); h->explicit_2f = v; }
+  else if (k == "coarse_2f") { if (v < 0 || v > 1) return bad(); h->coarse_2f = v; }
+  else if (k == "tol") { if (!(value > 0.0) || !(value < 1.0)) return bad(); h->P.tol = value; }
   else { h->err = "fp_set_option: unknown key " + k; return FP_ERR_INVALID; }
   h->gdirty = 1;
   return FP_OK;
@@ -2209,16 +2353,17 @@ void fp_destroy(fp_handle *h) {
 
 // =========================== projection without allocation ==========================
 // fp_apply_projection_noalloc: the coarse projection of fp_apply_projection for callers
-// that may not allocate device memory at call time -- for instance code that runs while a
-// CUDA stream is being captured into a graph, or an embedding runtime that owns every
-// allocation itself.  Its two scratch vectors (G^T v and (G^T G)^{-1} G^T v) live in the
+// that may not allocate device memory at call time -- an embedding application that has
+// reserved the device memory for its own pool, or a latency-bound loop that cannot take
+// cudaMalloc's implicit device synchronisation.  Its two scratch vectors (G^T v and (G^T G)^{-1} G^T v) live in the
 // file-scope array below instead of handle memory, so the call performs no cudaMalloc,
 // cudaFree or allocating library call.  The array is fixed at compile time:
 // kNoAllocMaxCoarse coarse unknowns (3 per floating subdomain, i.e. up to 8192 floating
 // subdomains), 2 * 24576 doubles = 384 KiB on every device that loads this library, held
 // until the process exits.  Host code cannot use the array's name as a device address; the
 // address is obtained with cudaGetSymbolAddress once per device, with that device current,
-// during the first call on the device.
+// during the first call on the device, and kept for the life of the process (a
+// cudaDeviceReset would make it stale, as it does every handle's memory).
 namespace {
 constexpr int kNoAllocMaxCoarse = 3 * 8192;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxCoarse];
@@ -2227,14 +2372,15 @@ double *g_noalloc_addr[128] = {nullptr};
 }  // namespace
 
 extern "C" fp_status fp_apply_projection_noalloc(fp_handle *h, const double *v, double *out) {
-  if (!h || !v || !out) return FP_ERR_INVALID;
-  if (h->stage < 2) { h->err = "fp_apply_projection_noalloc before fp_factor"; return FP_ERR_STATE; }
+  if (!h) return FP_ERR_INVALID;
   const Topology &T = h->T;
   if (T.nH > kNoAllocMaxCoarse) {
     h->err = "fp_apply_projection_noalloc: " + std::to_string(T.nH) + " coarse unknowns exceed the fixed scratch of " +
              std::to_string(kNoAllocMaxCoarse) + " (8192 floating subdomains); use fp_apply_projection";
     return FP_ERR_INVALID;
   }
+  if (!v || !out) { h->err = "fp_apply_projection_noalloc: NULL vector"; return FP_ERR_INVALID; }
+  if (h->stage < 2) { h->err = "fp_apply_projection_noalloc before fp_factor"; return FP_ERR_STATE; }
   int prev = -1;
   CK(cudaGetDevice(&prev));
   if (prev != h->device) CK(cudaSetDevice(h->device));
@@ -2259,7 +2405,7 @@ extern "C" fp_status fp_apply_projection_noalloc(fp_handle *h, const double *v, 
         scratch = g_noalloc_addr[h->device];
       }
       double *cy = scratch, *ca = scratch + kNoAllocMaxCoarse;
-      k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, cy, h->fl_zero);
+      k_Gt<<<(T.NF * 32 + 255) / 256, 256, 0, h->stream>>>(h->D, v, cy, h->fl_zero, nullptr);
       cudaError_t e = launch_gemv(h->Hinv, cy, ca, T.nH, h->fl_zero, h->stream);
       if (e != cudaSuccess) { h->err = std::string("kernel launch: ") + cudaGetErrorString(e); st = FP_ERR_CUDA; break; }
       k_Gcomb<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, ca, v, -1.0, out, h->fl_zero);

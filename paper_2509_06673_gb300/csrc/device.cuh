@@ -39,6 +39,7 @@ struct DevTopo {
   const int8_t *bsc_sign;
   // coarse
   const int *sub_float, *float_sub, *float_rows_ptr, *float_rows;
+  const double *float_g;             // [3 * float_rows] G entries of each (floating subdomain, row) pair
   const int *lam_fa, *lam_fb;        // floating index of s_a / s_b or -1
   const double *lam_ga, *lam_gb;     // [3 * nlam] G row entries for s_a / s_b
 };
@@ -69,6 +70,32 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Two-float ("double-float") arithmetic: a value is an unevaluated sum h + l of two floats.
+// Products and sums use error-free transformations (Knuth's TwoSum; TwoProduct by fma), in the
+// manner of Ogita, Rump & Oishi's Dot2: sums of a few hundred terms keep ~2^-46 relative error.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (h, l) += (bh, bl), renormalised
+__device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+// (h, l) = (ah + al) * (xh + xl), dropping al * xl (~2^-48 relative)
+__device__ __forceinline__ void df_mul(float ah, float al, float xh, float xl, float &h, float &l) {
+  h = ah * xh;
+  l = fmaf(ah, xh, -h) + fmaf(ah, xl, al * xh);
+}
+__device__ __forceinline__ void df_split(double v, float &h, float &l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
 // PCG state kept on the device: scalar slots, integer flags, reduction finalisers
 enum ScSlot { SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RNORM2, SC_REF2, SC_TOL2, SC_TMP, SC_TRUE2, SC_RMIN,
               SC_N = 16 };
@@ -76,8 +103,9 @@ enum ScSlot { SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RNORM2, SC_REF2, SC_TOL2, 
 // current WHILE loop, restarts taken, restart requested by the last true-residual check).
 // FL_STAG: iterations since the recursive residual last halved; FL_STAGWIN: the window after
 // which the loop stops for a restart (0: never); FL_NSTAG: such stops in this step.
+// FL_NINNER: executions of the inner loop body in this step (for the launch count).
 enum FlSlot { FL_DONE = 0, FL_ITER, FL_STATUS, FL_MAXIT, FL_IRSKIP, FL_IRSWEEPS, FL_BODY, FL_RESTARTS, FL_PENDING,
-              FL_STAG, FL_STAGWIN, FL_NSTAG, FL_N = 12 };
+              FL_STAG, FL_STAGWIN, FL_NSTAG, FL_NINNER, FL_N = 13 };
 // per-step scalars read by kernels from device memory (so one captured graph serves every
 // step): time t_n, extrapolation ratio rho of the source signal, squared tolerance
 enum StepSlot { ST_T = 0, ST_RHO, ST_TOL2, ST_N = 4 };

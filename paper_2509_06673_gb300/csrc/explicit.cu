@@ -295,8 +295,12 @@ __global__ void k_pack_sym(DevTopo D, const Tin *full, const long long *full_off
 // half of its values selected by bit k of its lane index and adds the partner's copy of that
 // half: 31 shuffles, and lane l ends with row sum l).  Partial sums land in shared memory and
 // are added in a fixed order.
+// With vlam given, x_b is formed here from the multiplier vector (x_b = B_s^T vlam, the fixed
+// dofs of a floating subdomain zero when skip_fixed), as k_scatter would, instead of being read
+// from the local vector: one launch and one pass over the rows b_s fewer per apply.
 __global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const float *tiles, const long long *tile_off,
-                                                            double *xloc, const int *fl) {
+                                                            double *xloc, const int *fl, const double *vlam,
+                                                            int skip_fixed) {
   if (fl && fl[FL_DONE]) return;
   extern __shared__ float smf[];
   const int s = blockIdx.x;
@@ -307,7 +311,25 @@ __global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const flo
   float *cp = rp + ntile * 32;     // ntile * 32 column-part sums
   const int *bnd = D.pool + t.bnd;
   double *x = xloc + D.vec_off[s];
-  for (int q = threadIdx.x; q < nt * 32; q += blockDim.x) xs[q] = q < m ? float(x[bnd[q]]) : 0.0f;
+  if (vlam) {
+    const long long b0 = D.bsc_off[s];
+    for (int q = threadIdx.x; q < nt * 32; q += blockDim.x) {
+      double acc = 0.0;
+      if (q < m) {
+        const int d = bnd[q];
+        if (!(skip_fixed && t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2))) {
+#pragma unroll
+          for (int z = 0; z < 3; ++z) {
+            const int r = D.bsc_row[3 * (b0 + q) + z];
+            if (r >= 0) acc += D.bsc_sign[3 * (b0 + q) + z] * vlam[r];
+          }
+        }
+      }
+      xs[q] = float(acc);
+    }
+  } else {
+    for (int q = threadIdx.x; q < nt * 32; q += blockDim.x) xs[q] = q < m ? float(x[bnd[q]]) : 0.0f;
+  }
   __syncthreads();
   const float *A = tiles + tile_off[s];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -350,6 +372,139 @@ __global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const flo
   }
 }
 
+// ------------------------- symmetric tiled two-float operators -------------------------
+// The accurate applies of the mixed-precision path (reference, initial, learned-guess and true
+// residuals) need F_s to FP64 accuracy.  F_s (formed in FP64) is kept as hi/lo FP32 pairs of its
+// upper 32 x 32 tiles (hi = fl32(a), lo = fl32(a - hi); 2048 floats per tile at 2 x the tile
+// offsets of the FP32 loop operator): the bytes of half the FP64 matrix, and FP32 arithmetic with
+// error-free products and sums (two-float; ~1e-14 relative) instead of FP64 FMAs, which bound the
+// FP64 apply on GB300.
+__global__ void k_pack_sym2f(DevTopo D, const double *full, const long long *full_off, float *tiles,
+                             const long long *tile_off) {
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int m = t.nbnd, mp = (m + 3) & ~3, nt = (m + 31) / 32, ntile = nt * (nt + 1) / 2;
+  const double *Fm = full + full_off[s];
+  float *Tm = tiles + 2 * tile_off[s];
+  for (long long idx = threadIdx.x; idx < (long long)ntile * 1024; idx += blockDim.x) {
+    int I, J;
+    const int tile = (int)(idx >> 10);
+    tile_ij(tile, nt, I, J);
+    const int e = (int)(idx & 1023), a = 32 * I + (e >> 5), j = 32 * J + (e & 31);
+    const double v = (a < m && j < m) ? Fm[(long long)a * mp + j] : 0.0;
+    float h, l;
+    df_split(v, h, l);
+    Tm[(long long)tile * 2048 + e] = h;
+    Tm[(long long)tile * 2048 + 1024 + e] = l;
+  }
+}
+
+// y_b = A_s x_b in two-float arithmetic, in place on the local vectors at the rows b_s: the
+// tile schedule of k_explicit_apply_sym (a warp per tile, lane c holding column c; transposed
+// product as a per-lane sum, direct product through the transposing butterfly), two-float
+// partials in shared memory added in a fixed order; one rounding to FP64 per row.
+__global__ void __launch_bounds__(256, 2) k_explicit_apply_sym2f(DevTopo D, const float *tiles,
+                                                                 const long long *tile_off, double *xloc,
+                                                                 const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  extern __shared__ float2 smd2[];
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int m = t.nbnd, nt = (m + 31) / 32, ntile = nt * (nt + 1) / 2;
+  float2 *rp = smd2;                 // ntile * 32 row-part sums (two-float)
+  float2 *cp = rp + ntile * 32;      // ntile * 32 column-part sums
+  float *xh = reinterpret_cast<float *>(cp + ntile * 32);  // nt * 32
+  float *xl = xh + nt * 32;
+  const int *bnd = D.pool + t.bnd;
+  double *x = xloc + D.vec_off[s];
+  for (int q = threadIdx.x; q < nt * 32; q += blockDim.x) {
+    float h = 0.0f, l = 0.0f;
+    if (q < m) df_split(x[bnd[q]], h, l);
+    xh[q] = h;
+    xl[q] = l;
+  }
+  __syncthreads();
+  const float *A = tiles + 2 * tile_off[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int tile = warp; tile < ntile; tile += nw) {
+    int I, J;
+    tile_ij(tile, nt, I, J);
+    const float *T = A + (long long)tile * 2048;
+    float vh[32], vl[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      vh[r] = T[r * 32 + lane];
+      vl[r] = T[1024 + r * 32 + lane];
+    }
+    if (I < J) {
+      float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        float ph, pl;
+        df_mul(vh[r], vl[r], xh[32 * I + r], xl[32 * I + r], ph, pl);
+        df_add(sh, sl, ph, pl);
+      }
+      cp[tile * 32 + lane] = make_float2(sh, sl);
+    }
+    const float yh = xh[32 * J + lane], yl = xl[32 * J + lane];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      float ph, pl;
+      df_mul(vh[r], vl[r], yh, yl, ph, pl);
+      vh[r] = ph;
+      vl[r] = pl;
+    }
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+      const bool up = (lane & k) != 0;
+#pragma unroll
+      for (int i = 0; i < k; ++i) {
+        const float sendh = up ? vh[i] : vh[i + k], sendl = up ? vl[i] : vl[i + k];
+        float kh = up ? vh[i + k] : vh[i], kl = up ? vl[i + k] : vl[i];
+        const float rh = __shfl_xor_sync(FULL, sendh, k), rl = __shfl_xor_sync(FULL, sendl, k);
+        df_add(kh, kl, rh, rl);
+        vh[i] = kh;
+        vl[i] = kl;
+      }
+    }
+    rp[tile * 32 + lane] = make_float2(vh[0], vl[0]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int I = i >> 5, r = i & 31;
+    const int row0 = I * nt - I * (I - 1) / 2;
+    float yh = 0.0f, yl = 0.0f;
+    for (int J = I; J < nt; ++J) {
+      const float2 q = rp[(row0 + J - I) * 32 + r];
+      df_add(yh, yl, q.x, q.y);
+    }
+    for (int I2 = 0; I2 < I; ++I2) {
+      const float2 q = cp[(I2 * nt - I2 * (I2 - 1) / 2 + I - I2) * 32 + r];
+      df_add(yh, yl, q.x, q.y);
+    }
+    x[bnd[i]] = (double)yh + (double)yl;
+  }
+}
+
+cudaError_t launch_pack_sym2f(DevTopo D, int S, const double *full, const long long *full_off, float *tiles,
+                              const long long *tile_off, cudaStream_t st) {
+  k_pack_sym2f<<<S, 256, 0, st>>>(D, full, full_off, tiles, tile_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_explicit_apply_sym2f(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
+                                        double *xloc, const int *fl, cudaStream_t st) {
+  const int nt = (mmax_bnd + 31) / 32;
+  const size_t smem = sizeof(float2) * (size_t)nt * (nt + 1) * 32 + sizeof(float) * 2 * (size_t)nt * 32;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_explicit_apply_sym2f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_explicit_apply_sym2f<<<S, 256, smem, st>>>(D, tiles, tile_off, xloc, fl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, const long long *full_off,
                             float *tiles, const long long *tile_off, cudaStream_t st) {
   if (src_fp64) k_pack_sym<double><<<S, 256, 0, st>>>(D, (const double *)full, full_off, tiles, tile_off);
@@ -358,14 +513,15 @@ cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, c
 }
 
 cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
-                                      double *xloc, const int *fl, cudaStream_t st) {
+                                      double *xloc, const int *fl, cudaStream_t st, const double *vlam,
+                                      int skip_fixed) {
   const int nt = (mmax_bnd + 31) / 32;
   const size_t smem = sizeof(float) * ((size_t)nt * 32 + (size_t)nt * (nt + 1) * 32);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_explicit_apply_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_explicit_apply_sym<<<S, 256, smem, st>>>(D, tiles, tile_off, xloc, fl);
+  k_explicit_apply_sym<<<S, 256, smem, st>>>(D, tiles, tile_off, xloc, fl, vlam, skip_fixed);
   return cudaGetLastError();
 }
 
@@ -389,7 +545,7 @@ size_t mrhs_smem_bytes(bool fp32, int R, int LDp, int mt) {
 }
 
 // rows per thread of the forward coupling for half bandwidth b: ceil(b / RG), RG = 256 / (MT / 4)
-static int mrhs_nr(int b, int mt) {
+int mrhs_nr(int b, int mt) {
   const int rg = 256 / (mt / 4);
   const int nr = (b + rg - 1) / rg;
   return nr <= 4 ? 4 : nr <= 8 ? 8 : nr <= 12 ? 12 : nr <= 16 ? 16 : 0;

@@ -38,13 +38,18 @@ __device__ bool finish_reduction(double local, double *partial, unsigned *counte
   }
   __syncthreads();
   if (!last) return false;
-  if (threadIdx.x == 0) {
+  // the last block's first warp adds the block partials: lane l takes partials l, l + 32, ...
+  // in order, then a butterfly (a fixed order, so the sum is reproducible)
+  if (threadIdx.x < 32) {
     __threadfence();
     double t = 0.0;
-    for (int i = 0; i < (int)gridDim.x; ++i) t += ((volatile double *)partial)[i];
-    total = t;
-    *counter = 0u;
-    return true;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) t += ((volatile double *)partial)[i];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) {
+      total = t;
+      *counter = 0u;
+      return true;
+    }
   }
   return false;
 }
@@ -183,6 +188,31 @@ __global__ void k_gather(DevTopo D, const double *xloc, double *out, const int *
   out[r] = xloc[D.vec_off[D.lam_sa[r]] + D.lam_da[r]] - xloc[D.vec_off[D.lam_sb[r]] + D.lam_db[r]];
 }
 
+// out = W (B x): the gather of k_gather followed by the scaling of k_wscale, one thread per
+// group of W (the rows of one node component), in one launch.
+__global__ void k_gather_wscale(DevTopo D, const double *xloc, double *out, const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= D.nwgrp) return;
+  const int f = D.wgrp_first[gidx], m = D.wgrp_size[gidx];
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < m; ++k) {
+    const int r = f + k;
+    g[k] = xloc[D.vec_off[D.lam_sa[r]] + D.lam_da[r]] - xloc[D.vec_off[D.lam_sb[r]] + D.lam_db[r]];
+  }
+  constexpr double third = 1.0 / 3.0;
+  if (m == 1) {
+    out[f] = 0.5 * g[0];
+  } else if (m == 2) {
+    out[f] = (2 * g[0] + g[1]) * third;
+    out[f + 1] = (g[0] + 2 * g[1]) * third;
+  } else {
+    out[f] = (3 * g[0] + 2 * g[1] + g[2]) * 0.25;
+    out[f + 1] = (2 * g[0] + 4 * g[1] + 2 * g[2]) * 0.25;
+    out[f + 2] = (g[0] + 2 * g[1] + 3 * g[2]) * 0.25;
+  }
+}
+
 // out = W v, W = (B B^T)^{-1}: per node component a chain of m-1 <= 3 rows whose B B^T is
 // tridiag(-1, 2, -1); its inverse in closed form.
 __global__ void k_wscale(DevTopo D, const double *v, double *out, const int *fl) {
@@ -190,17 +220,20 @@ __global__ void k_wscale(DevTopo D, const double *v, double *out, const int *fl)
   const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= D.nwgrp) return;
   const int f = D.wgrp_first[gidx], m = D.wgrp_size[gidx];
+  // multiplications by the constant reciprocals (GB300's FP64 divide is a long instruction
+  // sequence; 1/4 is exact, 1/3 rounds once)
+  constexpr double third = 1.0 / 3.0;
   if (m == 1) {
     out[f] = 0.5 * v[f];
   } else if (m == 2) {
     const double a = v[f], b = v[f + 1];
-    out[f] = (2 * a + b) / 3.0;
-    out[f + 1] = (a + 2 * b) / 3.0;
+    out[f] = (2 * a + b) * third;
+    out[f + 1] = (a + 2 * b) * third;
   } else {
     const double a = v[f], b = v[f + 1], c = v[f + 2];
-    out[f] = (3 * a + 2 * b + c) / 4.0;
-    out[f + 1] = (2 * a + 4 * b + 2 * c) / 4.0;
-    out[f + 2] = (a + 2 * b + 3 * c) / 4.0;
+    out[f] = (3 * a + 2 * b + c) * 0.25;
+    out[f + 1] = (2 * a + 4 * b + 2 * c) * 0.25;
+    out[f + 2] = (a + 2 * b + 3 * c) * 0.25;
   }
 }
 
@@ -335,21 +368,45 @@ __global__ void k_local_add(double *x, const double *r, long long n, const int *
 }
 
 // ------------------------------------ coarse -----------------------------------------
-// y = G^T v : one warp per floating subdomain, lanes stride over its rows, fixed-order sum.
-__global__ void k_Gt(DevTopo D, const double *v, double *y, const int *fl) {
+// float_g[3 q ..] = the G row entries (3 rigid modes) that row float_rows[q] has for the
+// floating subdomain owning entry q: one warp per floating subdomain (setup, after k_coarse_G)
+__global__ void k_pack_float_g(DevTopo D, double *fg) {
+  const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (f >= D.NF) return;
+  for (int q = D.float_rows_ptr[f] + lane; q < D.float_rows_ptr[f + 1]; q += 32) {
+    const int r = D.float_rows[q];
+    const double *g = (D.lam_fa[r] == f ? D.lam_ga : D.lam_gb) + 3 * (long long)r;
+    fg[3 * (long long)q] = g[0];
+    fg[3 * (long long)q + 1] = g[1];
+    fg[3 * (long long)q + 2] = g[2];
+  }
+}
+
+// y = G^T v : one warp per floating subdomain, lanes stride over its rows (entries packed per
+// subdomain: one index and three coefficients per row), fixed-order sum.
+__global__ void k_Gt(DevTopo D, const double *v, double *y, const int *fl, float *ysplit) {
   if (fl && fl[FL_DONE]) return;
   const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (f >= D.NF) return;
   double a0 = 0, a1 = 0, a2 = 0;
-  for (int q = D.float_rows_ptr[f] + lane; q < D.float_rows_ptr[f + 1]; q += 32) {
-    const int r = D.float_rows[q];
-    const double *g = (D.lam_fa[r] == f ? D.lam_ga : D.lam_gb) + 3 * (long long)r;
-    const double vr = v[r];
+  const int q1 = D.float_rows_ptr[f + 1];
+#pragma unroll 4
+  for (int q = D.float_rows_ptr[f] + lane; q < q1; q += 32) {
+    const double vr = v[D.float_rows[q]];
+    const double *g = D.float_g + 3 * (long long)q;
     a0 += g[0] * vr; a1 += g[1] * vr; a2 += g[2] * vr;
   }
   a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
   if (lane == 0) { y[3 * f] = a0; y[3 * f + 1] = a1; y[3 * f + 2] = a2; }
+  if (ysplit && lane < 3) {  // two-float copy (hi at [i], lo at [nH + i]) for the tiled product
+    const double a = lane == 0 ? a0 : lane == 1 ? a1 : a2;
+    float h, l;
+    df_split(a, h, l);
+    ysplit[3 * f + lane] = h;
+    ysplit[3 * D.NF + 3 * f + lane] = l;
+  }
 }
 
 // alpha = H y with H = (G^T G)^{-1} dense nH x nH (row-major, FP64): one warp per row, y
@@ -382,6 +439,147 @@ cudaError_t launch_gemv(const double *H, const double *y, double *alpha, int nH,
   return cudaGetLastError();
 }
 
+// ------------------- (G^T G)^{-1} y from two-float symmetric tiles ---------------------
+// The dense inverse H = (G^T G)^{-1} is symmetric.  Its upper 32 x 32 tiles (I <= J; tile
+// index start(I) + J - I, start(I) = I nt - I (I - 1) / 2, nt = ceil(nH / 32)) are stored as
+// two FP32 tiles, hi = fl32(h) and lo = fl32(h - hi) (2048 floats per tile, row-major, zero past
+// nH): half the bytes of the FP64 matrix, and the products run on FP32 units (GB300's FP64
+// rate, not HBM, bounds the FP64 product).  Products and sums use error-free transformations
+// (Knuth's TwoSum; TwoProduct by fma) in the manner of Ogita, Rump & Oishi's Dot2, so every
+// tile's partial sums carry ~2^-46 relative error; partials are added in FP64 in a fixed order.
+namespace {
+__device__ __forceinline__ int coarse_tile_row(int tile, int nt) {
+  // largest I with start(I) <= tile
+  const double b = 2.0 * nt + 1.0;
+  int I = (int)floor((b - sqrt(fmax(b * b - 8.0 * tile, 0.0))) * 0.5);
+  I = max(0, min(I, nt - 1));
+  while (I > 0 && I * nt - I * (I - 1) / 2 > tile) --I;
+  while (I + 1 < nt && (I + 1) * nt - (I + 1) * I / 2 <= tile) ++I;
+  return I;
+}
+}  // namespace
+
+// Packs the upper tiles of H (dense nH x nH FP64, row-major) into hi/lo FP32 tiles.
+__global__ void k_coarse_pack2f(const double *H, int nH, float *tiles) {
+  const int nt = (nH + 31) / 32;
+  const int tile = blockIdx.x;
+  const int I = coarse_tile_row(tile, nt);
+  const int J = I + tile - (I * nt - I * (I - 1) / 2);
+  float *T = tiles + (long long)tile * 2048;
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int a = 32 * I + (e >> 5), j = 32 * J + (e & 31);
+    const double v = (a < nH && j < nH) ? H[(long long)a * nH + j] : 0.0;
+    float h, l;
+    df_split(v, h, l);
+    T[e] = h;
+    T[1024 + e] = l;
+  }
+}
+
+// One warp per tile (I, J): lane c holds column c (coalesced 128-byte rows of hi and lo).
+// Direct product H_IJ y_J -> row block I through a transposing butterfly (as in the tiled
+// interface operators); transposed product H_IJ^T y_I -> row block J (I < J only) as per-lane
+// sums.  y comes pre-split into two floats (ys: hi at [i], lo at [nH + i]), so the kernel runs
+// no FP64 instruction; partials go to rp[tile] / cp[tile] as two-float pairs.
+__global__ void __launch_bounds__(256, 2) k_coarse_apply2f(const float *__restrict__ tiles, int nH,
+                                                           const float *__restrict__ ys, float2 *rp, float2 *cp,
+                                                           const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  const int nt = (nH + 31) / 32, ntile = nt * (nt + 1) / 2;
+  const int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (tile >= ntile) return;
+  const int I = coarse_tile_row(tile, nt);
+  const int J = I + tile - (I * nt - I * (I - 1) / 2);
+  const float *T = tiles + (long long)tile * 2048;
+  float vh[32], vl[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    vh[r] = __ldg(T + r * 32 + lane);
+    vl[r] = __ldg(T + 1024 + r * 32 + lane);
+  }
+  if (I < J) {
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int row = 32 * I + r;
+      const float xh = row < nH ? __ldg(ys + row) : 0.0f, xl = row < nH ? __ldg(ys + nH + row) : 0.0f;
+      float ph, pl;
+      df_mul(vh[r], vl[r], xh, xl, ph, pl);
+      df_add(sh, sl, ph, pl);
+    }
+    cp[(long long)tile * 32 + lane] = make_float2(sh, sl);
+  }
+  const int col = 32 * J + lane;
+  const float xh = col < nH ? __ldg(ys + col) : 0.0f, xl = col < nH ? __ldg(ys + nH + col) : 0.0f;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    float ph, pl;
+    df_mul(vh[r], vl[r], xh, xl, ph, pl);
+    vh[r] = ph;
+    vl[r] = pl;
+  }
+#pragma unroll
+  for (int k = 16; k >= 1; k >>= 1) {
+    const bool up = (lane & k) != 0;
+#pragma unroll
+    for (int i = 0; i < k; ++i) {
+      const float sendh = up ? vh[i] : vh[i + k], sendl = up ? vl[i] : vl[i + k];
+      float kh = up ? vh[i + k] : vh[i], kl = up ? vl[i + k] : vl[i];
+      const float rh = __shfl_xor_sync(FULL, sendh, k), rl = __shfl_xor_sync(FULL, sendl, k);
+      df_add(kh, kl, rh, rl);
+      vh[i] = kh;
+      vl[i] = kl;
+    }
+  }
+  rp[(long long)tile * 32 + lane] = make_float2(vh[0], vl[0]);
+}
+
+// alpha_i = sum_{J >= I} rp[(I, J)][r] + sum_{J < I} cp[(J, I)][r], i = 32 I + r: one block per
+// row block I, warp w takes J = w, w + 8, ... (coalesced rows of partials), two-float sums; the
+// eight warp sums are added in a fixed order, and the result is rounded once to FP64.
+__global__ void __launch_bounds__(256) k_coarse_sum2f(const float2 *rp, const float2 *cp, int nH, double *alpha,
+                                                     const int *fl) {
+  if (fl && fl[FL_DONE]) return;
+  __shared__ float2 part[8][32];
+  const int nt = (nH + 31) / 32, I = blockIdx.x, r = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long row0 = (long long)I * nt - (long long)I * (I - 1) / 2;
+  float ah = 0.0f, al = 0.0f;
+  for (int J = I + w; J < nt; J += 8) {
+    const float2 q = rp[(row0 + J - I) * 32 + r];
+    df_add(ah, al, q.x, q.y);
+  }
+  for (int J = w; J < I; J += 8) {
+    const float2 q = cp[((long long)J * nt - (long long)J * (J - 1) / 2 + I - J) * 32 + r];
+    df_add(ah, al, q.x, q.y);
+  }
+  part[w][r] = make_float2(ah, al);
+  __syncthreads();
+  if (w == 0) {
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) df_add(sh, sl, part[k][r].x, part[k][r].y);
+    const int i = 32 * I + r;
+    if (i < nH) alpha[i] = (double)sh + (double)sl;
+  }
+}
+
+cudaError_t launch_coarse_pack2f(const double *H, int nH, float *tiles, cudaStream_t st) {
+  const int nt = (nH + 31) / 32;
+  k_coarse_pack2f<<<nt * (nt + 1) / 2, 256, 0, st>>>(H, nH, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_apply2f(const float *tiles, int nH, const float *ysplit, double *part, double *alpha,
+                                  const int *fl, cudaStream_t st) {
+  const int nt = (nH + 31) / 32;
+  const long long ntile = (long long)nt * (nt + 1) / 2;
+  float2 *rp = reinterpret_cast<float2 *>(part), *cp = rp + ntile * 32;
+  k_coarse_apply2f<<<(unsigned)((ntile * 32 + 255) / 256), 256, 0, st>>>(tiles, nH, ysplit, rp, cp, fl);
+  k_coarse_sum2f<<<nt, 256, 0, st>>>(rp, cp, nH, alpha, fl);
+  return cudaGetLastError();
+}
+
 // out = v + sgn * G alpha  (v may be null)
 __global__ void k_Gcomb(DevTopo D, const double *alpha, const double *v, double sgn, double *out, const int *fl) {
   if (fl && fl[FL_DONE]) return;
@@ -392,6 +590,27 @@ __global__ void k_Gcomb(DevTopo D, const double *alpha, const double *v, double 
   if (fa >= 0) acc += D.lam_ga[3 * r] * alpha[3 * fa] + D.lam_ga[3 * r + 1] * alpha[3 * fa + 1] + D.lam_ga[3 * r + 2] * alpha[3 * fa + 2];
   if (fb >= 0) acc += D.lam_gb[3 * r] * alpha[3 * fb] + D.lam_gb[3 * r + 1] * alpha[3 * fb + 1] + D.lam_gb[3 * r + 2] * alpha[3 * fb + 2];
   out[r] = (v ? v[r] : 0.0) + sgn * acc;
+}
+
+// out = v - G alpha and dot(a, out) -> op in one launch (the projection's last step fused with
+// the reduction that follows it in Algorithm 1; the grid and the summation order are those of
+// k_dot, so the dot product is the same bit for bit).
+__global__ void k_Gcomb_dot(DevTopo D, const double *alpha, const double *v, double *out, const double *a,
+                            double *partial, unsigned *counter, double *sc, int *fl, int op) {
+  if (fl[FL_DONE]) return;
+  double s = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < D.nlam;
+       r += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    const int fa = D.lam_fa[r], fb = D.lam_fb[r];
+    if (fa >= 0) acc += D.lam_ga[3 * r] * alpha[3 * fa] + D.lam_ga[3 * r + 1] * alpha[3 * fa + 1] + D.lam_ga[3 * r + 2] * alpha[3 * fa + 2];
+    if (fb >= 0) acc += D.lam_gb[3 * r] * alpha[3 * fb] + D.lam_gb[3 * r + 1] * alpha[3 * fb + 1] + D.lam_gb[3 * r + 2] * alpha[3 * fb + 2];
+    const double o = v[r] - acc;
+    out[r] = o;
+    s += a[r] * o;
+  }
+  double tot;
+  if (finish_reduction(s, partial, counter, tot)) apply_op(op, tot, sc, fl);
 }
 
 // ------------------------------- right-hand side --------------------------------------
@@ -552,6 +771,7 @@ __global__ void k_loop_arm_inner(cudaGraphConditionalHandle hc, int *fl) {
 
 __global__ void k_loop_inner(cudaGraphConditionalHandle hc, int *fl, int max_body) {
   const int b = ++fl[FL_BODY];
+  fl[FL_NINNER] += 1;
   const bool more = !fl[FL_DONE] && fl[FL_ITER] < fl[FL_MAXIT] && b < max_body;
   cudaGraphSetConditional(hc, more ? 1u : 0u);
 }

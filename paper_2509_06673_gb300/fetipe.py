@@ -73,7 +73,9 @@ class Tuning(ctypes.Structure):
                 ("solve_ctas_per_sm", ctypes.c_int), ("factor_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("candidates", ctypes.c_int),
                 ("explicit_ms", ctypes.c_double), ("precond", ctypes.c_int),
-                ("precond_rate", ctypes.c_double * 2), ("precond_ms_per_it", ctypes.c_double * 2)]
+                ("precond_rate", ctypes.c_double * 2), ("precond_ms_per_it", ctypes.c_double * 2),
+                ("solve_mmax", ctypes.c_int), ("mrhs_nr", ctypes.c_int * 2), ("mrhs_mt", ctypes.c_int * 2),
+                ("mrhs_esz", ctypes.c_int * 2), ("factor_tc_ms", ctypes.c_double * 2)]
 
 
 class StepStats(ctypes.Structure):
@@ -82,7 +84,7 @@ class StepStats(ctypes.Structure):
                 ("lambda0_learned", ctypes.c_int), ("guess_res_prev", ctypes.c_double),
                 ("guess_res_learned", ctypes.c_double), ("restarts", ctypes.c_int),
                 ("stagnations", ctypes.c_int), ("h2d_bytes", ctypes.c_longlong),
-                ("d2h_bytes", ctypes.c_longlong)]
+                ("d2h_bytes", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong)]
 
 
 _vp = ctypes.c_void_p
@@ -182,6 +184,15 @@ def plan(case, precision=None, keys=False):
     return s, k
 
 
+def _current_cuda_device():
+    """The CUDA device current when a handle is created (the handle's device), if torch knows it."""
+    try:
+        import torch
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
 class Solver:
     """One fetipe handle.  ``case`` is a workloads.Case."""
 
@@ -192,6 +203,7 @@ class Solver:
         if st != FP_OK:
             raise FetipeError(st, _lib.fp_last_error(None).decode())
         self.case = case
+        self._device = _current_cuda_device()
         s = Sizes()
         self._check(_lib.fp_get_sizes(self._h, ctypes.byref(s)))
         self.sizes = s
@@ -227,7 +239,8 @@ class Solver:
                 "rel_residual": st.rel_residual, "true_rel_residual": st.true_rel_residual,
                 "lambda0_learned": st.lambda0_learned, "guess_res_prev": st.guess_res_prev,
                 "guess_res_learned": st.guess_res_learned, "restarts": st.restarts,
-                "stagnations": st.stagnations, "h2d_bytes": st.h2d_bytes, "d2h_bytes": st.d2h_bytes}
+                "stagnations": st.stagnations, "h2d_bytes": st.h2d_bytes, "d2h_bytes": st.d2h_bytes,
+                "kernel_launches": st.kernel_launches}
 
     def run(self, n_steps):
         st = StepStats()
@@ -299,7 +312,18 @@ class Solver:
         return self._op(_lib.fp_apply_projection, v)
 
     def apply_projection_noalloc(self, v, out):
-        """v, out: CUDA tensors (float64, n_lambda) on the handle's device."""
+        """fp_apply_projection_noalloc.  v, out: contiguous float64 CUDA tensors of n_lambda
+        entries on the handle's device (out may be v).  torch's current stream is synchronised
+        first, so that v is complete when the library's stream reads it."""
+        import torch
+        n = self.sizes.n_lambda
+        for name, t in (("v", v), ("out", out)):
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda \
+                    or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("%s must be a contiguous float64 CUDA tensor of %d entries" % (name, n))
+        if v.device != out.device or (self._device is not None and v.device.index != self._device):
+            raise ValueError("v and out must be on the handle's device (cuda:%s)" % self._device)
+        torch.cuda.current_stream(v.device).synchronize()
         self._check(_lib.fp_apply_projection_noalloc(self._h, v.data_ptr(), out.data_ptr()))
         return out
 
@@ -371,7 +395,7 @@ class Solver:
         t = Tuning()
         self._check(_lib.fp_get_tuning(self._h, ctypes.byref(t)))
         out = {k: getattr(t, k) for k, _ in Tuning._fields_}
-        for k in ("precond_rate", "precond_ms_per_it"):
+        for k in ("precond_rate", "precond_ms_per_it", "mrhs_nr", "mrhs_mt", "mrhs_esz", "factor_tc_ms"):
             out[k] = list(out[k])
         return out
 

@@ -82,3 +82,111 @@ def test_mixed_operator_accuracy(F):
     e0 = _rel(sol.apply_F(v), fe.F(v))
     assert 1e-12 < e0 < 1e-2   # plain FP32 solves: visibly less accurate, still close
     sol.close()
+
+
+@pytest.mark.parametrize("nsub, cells", [(8, 3), (16, 2)])
+def test_two_float_coarse_projection(F, nsub, cells):
+    """Mixed precision multiplies by (G^T G)^{-1} from hi/lo FP32 upper tiles with error-free
+    products and sums: P v agrees with the oracle's FP64 projector (and with the library's FP64
+    dense product, option coarse_2f = 0) to 1e-12, with 36 and 196 floating subdomains
+    (coarse orders 108 and 588: several 32 x 32 tile rows and a ragged last one)."""
+    from oracle.monolithic import Discretization
+    from oracle.feti import FETI
+    case = W.small_case(nsub, nsub, cells, k=1, lame_lambda=49.0, tau=1e-3, precision="mixed")
+    sol = F.Solver(case)
+    sol.assemble()
+    sol.factor()
+    assert sol.sizes.n_floating == (nsub - 2) ** 2
+    fe = FETI(case, Discretization(case))
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        v = rng.normal(size=sol.sizes.n_lambda)
+        got = sol.apply_projection(v)
+        assert _rel(got, fe.P(v)) < 1e-12
+        sol.set_option("coarse_2f", 0)
+        ref = sol.apply_projection(v)
+        sol.set_option("coarse_2f", 1)
+        assert _rel(got, ref) < 1e-12
+        # the projector's defining property: G^T P v = 0 (P v orthogonal to range(G))
+        G = fe.I.G
+        assert np.abs(G.T @ got).max() < 1e-11 * np.abs(G.T @ v).max()
+    sol.close()
+
+
+# half bandwidths 75 (one 128-row tile) and 175 (two, as on the large workload's 24 x 24 cells)
+TC_CASES = [CASES[1], W.small_case(3, 4, 16, k=2, lame_lambda=49.0, tau=1e-3, precision="mixed",
+                                   source="manufactured_t")]
+
+
+@pytest.mark.parametrize("case", TC_CASES)
+def test_tensor_core_factorisation(F, case):
+    """FP32 band factors with the trailing updates on the tensor cores (tcgen05 TF32 tiles, 3xTF32
+    split) against the CUDA-core FP32 factorisation and the oracle: the unrefined local solves of
+    both are equally close to the FP64 F and Dirichlet preconditioner, and the refined F apply
+    meets the FP64 bar."""
+    from oracle.monolithic import Discretization
+    from oracle.feti import FETI
+    fe = FETI(case, Discretization(case))
+    v = np.random.default_rng(5).normal(size=fe.I.n_lambda)
+    errs = {}
+    for tc in (1, 0):
+        sol = F.Solver(case)
+        sol.set_option("factor_fp64", 0)
+        sol.set_option("factor_tc", tc)
+        sol.assemble()
+        sol.factor()
+        ms = sol.tuning()["factor_tc_ms"]
+        assert (ms[0] > 0 and ms[1] > 0) == bool(tc)
+        assert _rel(sol.apply_F(v), fe.F(v)) < 1e-9
+        sol.set_option("ir_sweeps", 0)
+        errs[tc] = (_rel(sol.apply_F(v), fe.F(v)), _rel(sol.apply_precond(v), fe.precond(v)))
+        sol.close()
+    for k in range(2):
+        assert errs[1][k] < 1e-2 and errs[1][k] < 20 * errs[0][k] + 1e-12, errs
+
+
+def test_tensor_core_factorisation_steps(F):
+    """Both FP32 factors on the tensor cores (factor_fp64 = 0): steps match the oracle at 1e-8."""
+    from oracle.monolithic import Discretization, solve_monolithic
+    case = CASES[0]
+    mono = solve_monolithic(case, Discretization(case))
+    sol = F.Solver(case)
+    sol.set_option("factor_fp64", 0)
+    sol.set_option("ir_eps", 1e-15)
+    sol.assemble()
+    sol.factor()
+    assert min(sol.tuning()["factor_tc_ms"]) > 0
+    for n in range(case.n_steps):
+        st = sol.step()
+        assert st["true_rel_residual"] <= case.tol
+        assert _rel(sol.get_lambda(), mono[n]["lambda"]) < TOL, n
+        for s, (gu, gxi, geta, gp) in enumerate(F.split_fields(case, *sol.get_fields())):
+            u, xi, eta, p = mono[n]["fields"][s]
+            assert np.abs(gu - u).max() < TOL * np.abs(u).max(), (n, s)
+            if eta is not None:
+                assert np.abs(gp - p).max() < TOL * max(np.abs(p).max(), 1e-300), (n, s)
+    sol.close()
+
+
+def test_two_float_explicit_accurate_apply(F):
+    """With explicit operators, the accurate F applies of mixed precision multiply by F_s kept
+    as hi/lo FP32 symmetric tiles (two-float arithmetic): F v agrees with the oracle's FP64 F
+    and with the FP64 F_s product (explicit_2f = 0) to 1e-12."""
+    from oracle.monolithic import Discretization
+    from oracle.feti import FETI
+    case = CASES[1]
+    sol = F.Solver(case)
+    sol.set_option("explicit", 1)
+    sol.assemble()
+    sol.factor()
+    fe = FETI(case, Discretization(case))
+    rng = np.random.default_rng(4)
+    for _ in range(2):
+        v = rng.normal(size=sol.sizes.n_lambda)
+        got = sol.apply_F(v)
+        assert _rel(got, fe.F(v)) < 1e-12
+        sol.set_option("explicit_2f", 0)
+        ref = sol.apply_F(v)
+        sol.set_option("explicit_2f", 1)
+        assert _rel(got, ref) < 1e-12
+    sol.close()
