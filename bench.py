@@ -282,15 +282,25 @@ def _errors(F, smp, sol, ref):
     return out
 
 
+def arm_options(args, precision):
+    """The library options an arm runs with (the same on the full workload and on the sample)."""
+    if precision == "fp64":
+        opts = (("explicit", args.fp64_explicit), ("graph", args.graph))
+    else:
+        opts = (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
+                ("factor_fp64", args.factor_fp64), ("graph", args.graph), ("factor_nb", args.factor_nb),
+                ("explicit", args.explicit), ("precond_bf16", args.precond_bf16))
+    return [(k, v) for k, v in opts if v is not None]
+
+
 def sample_errors(F, smp, mono, precision, tol, args, stream):
     """The library on the sample under one arm's bench settings at tolerance `tol`: the same
     options, learned-guess recording and training, warm-up and step count as the timed run on
     the full workload.  Returns the max relative error per field over the timed step numbers."""
     case = smp.with_(precision=precision, tol=tol)
     sol = F.Solver(case, stream=stream.cuda_stream)
-    sol.set_option("explicit", args.explicit if precision == "mixed" else args.fp64_explicit)
-    if args.graph is not None:
-        sol.set_option("graph", args.graph)
+    for key, val in arm_options(args, precision):
+        sol.set_option(key, val)
     sol.assemble()
     sol.factor()
     learned = bool(args.learned) and precision == "mixed"
@@ -431,11 +441,8 @@ def run_native(args):
 
     # ---- the headline arm ---------------------------------------------------------------
     sol = F.Solver(case, stream=stream.cuda_stream)
-    for key, val in (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
-                     ("factor_fp64", args.factor_fp64), ("graph", args.graph), ("factor_nb", args.factor_nb),
-                     ("explicit", args.explicit)):
-        if val is not None:
-            sol.set_option(key, val)
+    for key, val in arm_options(args, case.precision):
+        sol.set_option(key, val)
     t0 = time.perf_counter()
     sol.assemble()
     sol.factor()
@@ -587,8 +594,8 @@ def run_native(args):
         # warm-up and tolerance policy
         c64 = case.with_(precision="fp64")
         s64 = F.Solver(c64, stream=stream.cuda_stream)
-        if args.fp64_explicit is not None:
-            s64.set_option("explicit", args.fp64_explicit)
+        for key, val in arm_options(args, "fp64"):
+            s64.set_option(key, val)
         t0 = time.perf_counter()
         s64.assemble()
         s64.factor()
@@ -743,6 +750,7 @@ def main():
     ap.add_argument("--precond", default=None, choices=[None, "dirichlet", "lumped", "auto"],
                     help="preconditioner (both arms); default: the workload's (Dirichlet)")
     ap.add_argument("--fp64-explicit", type=int, default=1, help="explicit operators in the FP64 arm")
+    ap.add_argument("--precond-bf16", type=int, default=None, help="mixed arm: S_s tiles in BF16")
     ap.add_argument("--graph", type=int, default=None, help="1: one CUDA graph launch per time step")
     ap.add_argument("--learned", type=int, default=1, help="mixed arm: learned lambda_0 (trained in warm-up)")
     ap.add_argument("--learned-epochs", type=int, default=8)

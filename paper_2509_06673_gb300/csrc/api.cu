@@ -45,10 +45,10 @@ cudaError_t launch_pack_sym2f(DevTopo D, int S, const double *full, const long l
 cudaError_t launch_explicit_apply_sym2f(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
                                         double *xloc, const int *fl, cudaStream_t st);
 cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, const long long *full_off,
-                            float *tiles, const long long *tile_off, cudaStream_t st);
-cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
+                            void *tiles, const long long *tile_off, cudaStream_t st, bool bf16_out = false);
+cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const void *tiles, const long long *tile_off,
                                       double *xloc, const int *fl, cudaStream_t st, const double *vlam,
-                                      int skip_fixed);
+                                      int skip_fixed, bool bf16);
 __global__ void k_gather_wscale(DevTopo, const double *, double *, const int *);
 __global__ void k_Gcomb_dot(DevTopo, const double *, const double *, double *, const double *, double *, unsigned *,
                             double *, int *, int);
@@ -157,6 +157,8 @@ struct fp_handle {
   double *opF64 = nullptr;              // mixed precision: F_s in FP64 for the accurate applies
   float *opF2 = nullptr;                // ... and as two-float (hi/lo FP32) symmetric tiles
   int explicit_2f = 1;                  // option: accurate mixed-precision F applies from opF2
+  int precond_bf16 = 0;                 // option: mixed precision's S_s tiles in BF16
+  int opS_bf16 = 0;                     // the stored S_s tiles are BF16
   const long long *op_off = nullptr, *tile_off = nullptr, *linv_off_dev = nullptr;
   long long op_total = 0, tile_total = 0;
   const int *mrhs_s[2] = {}, *mrhs_j0[2] = {};  // build tasks for tiles of 32 / 16 right-hand sides
@@ -706,8 +708,7 @@ fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, boo
   }
   if (op) {
     if (fused)
-      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)op, h->tile_off, h->XB, fl, h->stream,
-                                   v, 1));
+      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, op, h->tile_off, h->XB, fl, h->stream, v, 1, false));
     else if (mixed && h->opF2 && h->explicit_2f)
       CK(launch_explicit_apply_sym2f(h->D, h->T.S, h->nbnd_max, h->opF2, h->tile_off, h->XB, fl, h->stream));
     else
@@ -745,8 +746,8 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
   CKL();
   if (h->ops_ready) {
     if (fused) {
-      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, (const float *)h->opS, h->tile_off, h->XP, fl,
-                                   h->stream, h->t1, 0));
+      CK(launch_explicit_apply_sym(h->D, h->T.S, h->nbnd_max, h->opS, h->tile_off, h->XP, fl, h->stream, h->t1, 0,
+                                   h->opS_bf16 != 0));
       k_gather_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, out, fl);
       CKL();
       return FP_OK;
@@ -1175,8 +1176,10 @@ fp_status build_explicit(fp_handle *h) {
     }
   }
   if (st == FP_OK && need_S) st = run_mrhs(h, true, h->facD, h->linvD, 1, full);
+  h->opS_bf16 = h->precond_bf16;
   if (st == FP_OK && need_S &&
-      launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opS, h->tile_off, h->stream) != cudaSuccess) {
+      launch_pack_sym(false, h->D, h->T.S, full, h->op_off, h->opS, h->tile_off, h->stream, h->opS_bf16 != 0) !=
+          cudaSuccess) {
     h->err = "explicit operators: packing the symmetric tiles of S_s failed";
     st = FP_ERR_CUDA;
   }
@@ -2294,6 +2297,7 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "explicit_tile") { if (v != 0 && v != 16 && v != 32) return bad(); h->explicit_tile = v; }
   else if (k == "autotune") { if (v < 0 || v > 1) return bad(); h->autotune = v; }
   else if (k == "factor_tc") { if (v < 0 || v > 1) return bad(); h->factor_tc = v; }
+  else if (k == "precond_bf16") { if (v < 0 || v > 1) return bad(); h->precond_bf16 = v; }
   else if (k == "explicit_2f") { if (v < 0 || v > 1) return bad(); h->explicit_2f = v; }
   else if (k == "coarse_2f") { if (v < 0 || v > 1) return bad(); h->coarse_2f = v; }
   else if (k == "tol") { if (!(value > 0.0) || !(value < 1.0)) return bad(); h->P.tol = value; }

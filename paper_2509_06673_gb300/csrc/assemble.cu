@@ -360,13 +360,14 @@ __global__ void k_coarse_G(DevTopo D, double *ga, double *gb) {
     if (field > 1) continue;
     const int node = D.pool[t.dof_node + d];
     const double hx = D.sub_hx[s], hy = D.sub_hy[s];
-    const double x = D.sub_x0[s] + (node % t.nux) * hx / t.k;
-    const double y = D.sub_y0[s] + (node / t.nux) * hy / t.k;
+    // the same arithmetic as the rigid modes of the right-hand side and the recovery
+    const double hxk = hx / t.k, hyk = hy / t.k, invL = 1.0 / fmax(t.nx * hx, t.ny * hy);
+    const double x = D.sub_x0[s] + (node % t.nux) * hxk;
+    const double y = D.sub_y0[s] + (node / t.nux) * hyk;
     const double xc = D.sub_x0[s] + 0.5 * t.nx * hx, yc = D.sub_y0[s] + 0.5 * t.ny * hy;
-    const double L = fmax(t.nx * hx, t.ny * hy);
     const double sg = side == 0 ? 1.0 : -1.0;
-    if (field == 0) { g[0] = sg; g[2] = -sg * (y - yc) / L; }
-    else { g[1] = sg; g[2] = sg * (x - xc) / L; }
+    if (field == 0) { g[0] = sg; g[2] = -sg * (y - yc) * invL; }
+    else { g[1] = sg; g[2] = sg * (x - xc) * invL; }
   }
 }
 

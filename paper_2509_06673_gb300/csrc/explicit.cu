@@ -13,6 +13,7 @@
 // columns per thread in the forward sweep, 1 row x 4 columns in the backward sweep).
 // No spin-waits and no asynchronous copies: plain loads and __syncthreads only.
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -272,19 +273,24 @@ __device__ __forceinline__ void tile_ij(int tile, int nt, int &I, int &J) {
   J = I + tile;
 }
 
-template <typename Tin>
-__global__ void k_pack_sym(DevTopo D, const Tin *full, const long long *full_off, float *tiles,
+__device__ __forceinline__ void store_tile_elem(float *p, float v) { *p = v; }
+__device__ __forceinline__ void store_tile_elem(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ float load_tile_elem(const float *p) { return *p; }
+__device__ __forceinline__ float load_tile_elem(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+template <typename Tin, typename Tout>
+__global__ void k_pack_sym(DevTopo D, const Tin *full, const long long *full_off, Tout *tiles,
                            const long long *tile_off) {
   const int s = blockIdx.x;
   const DevTpl t = D.tpl[D.sub_tpl[s]];
   const int m = t.nbnd, mp = (m + 3) & ~3, nt = (m + 31) / 32, ntile = nt * (nt + 1) / 2;
   const Tin *Fm = full + full_off[s];
-  float *Tm = tiles + tile_off[s];
+  Tout *Tm = tiles + tile_off[s];
   for (long long idx = threadIdx.x; idx < (long long)ntile * 1024; idx += blockDim.x) {
     int I, J;
     tile_ij((int)(idx >> 10), nt, I, J);
     const int e = (int)(idx & 1023), a = 32 * I + (e >> 5), j = 32 * J + (e & 31);
-    Tm[idx] = (a < m && j < m) ? float(Fm[(long long)a * mp + j]) : 0.0f;
+    store_tile_elem(Tm + idx, (a < m && j < m) ? float(Fm[(long long)a * mp + j]) : 0.0f);
   }
 }
 
@@ -298,7 +304,10 @@ __global__ void k_pack_sym(DevTopo D, const Tin *full, const long long *full_off
 // With vlam given, x_b is formed here from the multiplier vector (x_b = B_s^T vlam, the fixed
 // dofs of a floating subdomain zero when skip_fixed), as k_scatter would, instead of being read
 // from the local vector: one launch and one pass over the rows b_s fewer per apply.
-__global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const float *tiles, const long long *tile_off,
+// TS: the tiles' storage type (FP32, or BF16 for the preconditioner's S_s: half the bytes; the
+// products and sums stay FP32).
+template <typename TS>
+__global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const TS *tiles, const long long *tile_off,
                                                             double *xloc, const int *fl, const double *vlam,
                                                             int skip_fixed) {
   if (fl && fl[FL_DONE]) return;
@@ -331,15 +340,15 @@ __global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const flo
     for (int q = threadIdx.x; q < nt * 32; q += blockDim.x) xs[q] = q < m ? float(x[bnd[q]]) : 0.0f;
   }
   __syncthreads();
-  const float *A = tiles + tile_off[s];
+  const TS *A = tiles + tile_off[s];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int tile = warp; tile < ntile; tile += nw) {
     int I, J;
     tile_ij(tile, nt, I, J);
-    const float *T = A + (long long)tile * 1024;
+    const TS *T = A + (long long)tile * 1024;
     float v[32];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = T[r * 32 + lane];
+    for (int r = 0; r < 32; ++r) v[r] = load_tile_elem(T + r * 32 + lane);
     if (I < J) {
       float acc = 0.0f;
 #pragma unroll
@@ -505,23 +514,42 @@ cudaError_t launch_explicit_apply_sym2f(DevTopo D, int S, int mmax_bnd, const fl
   return cudaGetLastError();
 }
 
+// bf16_out: tiles are BF16 (tiles points to tile_total BF16 values), else FP32
 cudaError_t launch_pack_sym(bool src_fp64, DevTopo D, int S, const void *full, const long long *full_off,
-                            float *tiles, const long long *tile_off, cudaStream_t st) {
-  if (src_fp64) k_pack_sym<double><<<S, 256, 0, st>>>(D, (const double *)full, full_off, tiles, tile_off);
-  else k_pack_sym<float><<<S, 256, 0, st>>>(D, (const float *)full, full_off, tiles, tile_off);
+                            void *tiles, const long long *tile_off, cudaStream_t st, bool bf16_out) {
+  if (bf16_out) {
+    __nv_bfloat16 *tb = (__nv_bfloat16 *)tiles;
+    if (src_fp64) k_pack_sym<double><<<S, 256, 0, st>>>(D, (const double *)full, full_off, tb, tile_off);
+    else k_pack_sym<float><<<S, 256, 0, st>>>(D, (const float *)full, full_off, tb, tile_off);
+  } else {
+    float *tf = (float *)tiles;
+    if (src_fp64) k_pack_sym<double><<<S, 256, 0, st>>>(D, (const double *)full, full_off, tf, tile_off);
+    else k_pack_sym<float><<<S, 256, 0, st>>>(D, (const float *)full, full_off, tf, tile_off);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const float *tiles, const long long *tile_off,
+cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const void *tiles, const long long *tile_off,
                                       double *xloc, const int *fl, cudaStream_t st, const double *vlam,
-                                      int skip_fixed) {
+                                      int skip_fixed, bool bf16) {
   const int nt = (mmax_bnd + 31) / 32;
   const size_t smem = sizeof(float) * ((size_t)nt * 32 + (size_t)nt * (nt + 1) * 32);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_explicit_apply_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  if (bf16) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_explicit_apply_sym<__nv_bfloat16>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_explicit_apply_sym<__nv_bfloat16><<<S, 256, smem, st>>>(D, (const __nv_bfloat16 *)tiles, tile_off, xloc, fl,
+                                                              vlam, skip_fixed);
+  } else {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_explicit_apply_sym<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_explicit_apply_sym<float><<<S, 256, smem, st>>>(D, (const float *)tiles, tile_off, xloc, fl, vlam, skip_fixed);
   }
-  k_explicit_apply_sym<<<S, 256, smem, st>>>(D, tiles, tile_off, xloc, fl, vlam, skip_fixed);
   return cudaGetLastError();
 }
 

@@ -476,12 +476,15 @@ __global__ void k_coarse_pack2f(const double *H, int nH, float *tiles) {
   }
 }
 
-// One warp per tile (I, J): lane c holds column c (coalesced 128-byte rows of hi and lo).
-// Direct product H_IJ y_J -> row block I through a transposing butterfly (as in the tiled
-// interface operators); transposed product H_IJ^T y_I -> row block J (I < J only) as per-lane
-// sums.  y comes pre-split into two floats (ys: hi at [i], lo at [nH + i]), so the kernel runs
-// no FP64 instruction; partials go to rp[tile] / cp[tile] as two-float pairs.
-__global__ void __launch_bounds__(256, 2) k_coarse_apply2f(const float *__restrict__ tiles, int nH,
+// One warp per tile (I, J): lane c holds column c (coalesced 128-byte rows of hi and lo), the
+// tile taken in two halves of 16 rows (half the registers of a whole tile: more warps per SM to
+// cover the memory latency).  Direct product H_IJ y_J -> row block I: per half a transposing
+// butterfly over 16 values (offsets 16, 8, 4, 2; lane l ends with row l >> 1 of the half, summed
+// over 16 lanes) and a final exchange with lane l ^ 1.  Transposed product H_IJ^T y_I -> row block
+// J (I < J only) as per-lane sums.  y comes pre-split into two floats (ys: hi at [i], lo at
+// [nH + i]), so the kernel runs no FP64 instruction; partials go to rp[tile] / cp[tile] as
+// two-float pairs.
+__global__ void __launch_bounds__(256, 4) k_coarse_apply2f(const float *__restrict__ tiles, int nH,
                                                            const float *__restrict__ ys, float2 *rp, float2 *cp,
                                                            const int *fl) {
   if (fl && fl[FL_DONE]) return;
@@ -492,47 +495,54 @@ __global__ void __launch_bounds__(256, 2) k_coarse_apply2f(const float *__restri
   const int I = coarse_tile_row(tile, nt);
   const int J = I + tile - (I * nt - I * (I - 1) / 2);
   const float *T = tiles + (long long)tile * 2048;
-  float vh[32], vl[32];
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    vh[r] = __ldg(T + r * 32 + lane);
-    vl[r] = __ldg(T + 1024 + r * 32 + lane);
-  }
-  if (I < J) {
-    float sh = 0.0f, sl = 0.0f;
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int row = 32 * I + r;
-      const float xh = row < nH ? __ldg(ys + row) : 0.0f, xl = row < nH ? __ldg(ys + nH + row) : 0.0f;
-      float ph, pl;
-      df_mul(vh[r], vl[r], xh, xl, ph, pl);
-      df_add(sh, sl, ph, pl);
-    }
-    cp[(long long)tile * 32 + lane] = make_float2(sh, sl);
-  }
   const int col = 32 * J + lane;
-  const float xh = col < nH ? __ldg(ys + col) : 0.0f, xl = col < nH ? __ldg(ys + nH + col) : 0.0f;
+  const float yh = col < nH ? __ldg(ys + col) : 0.0f, yl = col < nH ? __ldg(ys + nH + col) : 0.0f;
+  float sh = 0.0f, sl = 0.0f;  // transposed product, column `lane`
 #pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    float ph, pl;
-    df_mul(vh[r], vl[r], xh, xl, ph, pl);
-    vh[r] = ph;
-    vl[r] = pl;
-  }
+  for (int half = 0; half < 2; ++half) {
+    float vh[16], vl[16];
 #pragma unroll
-  for (int k = 16; k >= 1; k >>= 1) {
-    const bool up = (lane & k) != 0;
-#pragma unroll
-    for (int i = 0; i < k; ++i) {
-      const float sendh = up ? vh[i] : vh[i + k], sendl = up ? vl[i] : vl[i + k];
-      float kh = up ? vh[i + k] : vh[i], kl = up ? vl[i + k] : vl[i];
-      const float rh = __shfl_xor_sync(FULL, sendh, k), rl = __shfl_xor_sync(FULL, sendl, k);
-      df_add(kh, kl, rh, rl);
-      vh[i] = kh;
-      vl[i] = kl;
+    for (int i = 0; i < 16; ++i) {
+      vh[i] = __ldg(T + (16 * half + i) * 32 + lane);
+      vl[i] = __ldg(T + 1024 + (16 * half + i) * 32 + lane);
     }
+    if (I < J) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int row = 32 * I + 16 * half + i;
+        const float xh = row < nH ? __ldg(ys + row) : 0.0f, xl = row < nH ? __ldg(ys + nH + row) : 0.0f;
+        float ph, pl;
+        df_mul(vh[i], vl[i], xh, xl, ph, pl);
+        df_add(sh, sl, ph, pl);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float ph, pl;
+      df_mul(vh[i], vl[i], yh, yl, ph, pl);
+      vh[i] = ph;
+      vl[i] = pl;
+    }
+#pragma unroll
+    for (int k = 16, cnt = 8; k >= 2; k >>= 1, cnt >>= 1) {
+      const bool up = (lane & k) != 0;
+#pragma unroll
+      for (int i = 0; i < cnt; ++i) {
+        const float sendh = up ? vh[i] : vh[i + cnt], sendl = up ? vl[i] : vl[i + cnt];
+        float kh = up ? vh[i + cnt] : vh[i], kl = up ? vl[i + cnt] : vl[i];
+        const float rh = __shfl_xor_sync(FULL, sendh, k), rl = __shfl_xor_sync(FULL, sendl, k);
+        df_add(kh, kl, rh, rl);
+        vh[i] = kh;
+        vl[i] = kl;
+      }
+    }
+    {
+      const float rh = __shfl_xor_sync(FULL, vh[0], 1), rl = __shfl_xor_sync(FULL, vl[0], 1);
+      df_add(vh[0], vl[0], rh, rl);
+    }
+    if ((lane & 1) == 0) rp[(long long)tile * 32 + 16 * half + (lane >> 1)] = make_float2(vh[0], vl[0]);
   }
-  rp[(long long)tile * 32 + lane] = make_float2(vh[0], vl[0]);
+  if (I < J) cp[(long long)tile * 32 + lane] = make_float2(sh, sl);
 }
 
 // alpha_i = sum_{J >= I} rp[(I, J)][r] + sum_{J < I} cp[(J, I)][r], i = 32 I + r: one block per
@@ -633,7 +643,8 @@ __global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double 
   const int fidx = D.sub_float[s];
   const double hx = D.sub_hx[s], hy = D.sub_hy[s];
   const double xc = D.sub_x0[s] + 0.5 * t.nx * hx, yc = D.sub_y0[s] + 0.5 * t.ny * hy;
-  const double L = fmax(t.nx * hx, t.ny * hy);
+  // node spacing and 1 / L once per subdomain (GB300's FP64 divide is a long sequence)
+  const double hxk = hx / t.k, hyk = hy / t.k, invL = 1.0 / fmax(t.nx * hx, t.ny * hy);
   double e0 = 0, e1 = 0, e2 = 0;
   for (int d = threadIdx.x; d < t.n; d += blockDim.x) {
     const int f = dfield[d], node = dnode[d];
@@ -641,10 +652,11 @@ __global__ void k_rhs(DevTopo D, DevParams P, const double *fstat, const double 
     if (f <= 1) {
       v = g * fs[d];
       if (fidx >= 0) {
-        const double xx = D.sub_x0[s] + (node % t.nux) * hx / t.k;
-        const double yy = D.sub_y0[s] + (node / t.nux) * hy / t.k;
-        if (f == 0) { e0 += v; e2 += -(yy - yc) / L * v; }
-        else { e1 += v; e2 += (xx - xc) / L * v; }
+        const int ni = node % t.nux, nj = node / t.nux;
+        const double xx = D.sub_x0[s] + ni * hxk;
+        const double yy = D.sub_y0[s] + nj * hyk;
+        if (f == 0) { e0 += v; e2 += -(yy - yc) * invL * v; }
+        else { e1 += v; e2 += (xx - xc) * invL * v; }
       }
     } else if (f == 3) {
       double z = g * Zn[pn0 + node] + dg * E0n[pn0 + node];
@@ -676,7 +688,7 @@ __global__ void k_recover(DevTopo D, DevParams P, const double *xf, const double
   const int fidx = D.sub_float[s];
   const double hx = D.sub_hx[s], hy = D.sub_hy[s];
   const double xc = D.sub_x0[s] + 0.5 * t.nx * hx, yc = D.sub_y0[s] + 0.5 * t.ny * hy;
-  const double L = fmax(t.nx * hx, t.ny * hy);
+  const double hxk = hx / t.k, hyk = hy / t.k, invL = 1.0 / fmax(t.nx * hx, t.ny * hy);
   // Dirichlet nodes carry the (homogeneous) boundary data: zero everything first
   for (int i = threadIdx.x; i < 2 * t.nux * t.nuy; i += blockDim.x) U[2 * un0 + i] = 0.0;
   for (int i = threadIdx.x; i < t.npx * t.npy; i += blockDim.x) {
@@ -689,11 +701,11 @@ __global__ void k_recover(DevTopo D, DevParams P, const double *xf, const double
     double v = a[d] - b[d];
     if (f <= 1) {
       if (fidx >= 0) {
-        const double xx = D.sub_x0[s] + (node % t.nux) * hx / t.k;
-        const double yy = D.sub_y0[s] + (node / t.nux) * hy / t.k;
+        const double xx = D.sub_x0[s] + (node % t.nux) * hxk;
+        const double yy = D.sub_y0[s] + (node / t.nux) * hyk;
         const double *al = alpha + 3 * fidx;
-        if (f == 0) v += al[0] - (yy - yc) / L * al[2];
-        else v += al[1] + (xx - xc) / L * al[2];
+        if (f == 0) v += al[0] - (yy - yc) * invL * al[2];
+        else v += al[1] + (xx - xc) * invL * al[2];
       }
       U[2 * (un0 + node) + f] = v;
     } else if (f == 2) {

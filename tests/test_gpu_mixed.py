@@ -190,3 +190,33 @@ def test_two_float_explicit_accurate_apply(F):
         sol.set_option("explicit_2f", 1)
         assert _rel(got, ref) < 1e-12
     sol.close()
+
+
+def test_bf16_preconditioner_steps(F):
+    """The Dirichlet preconditioner's S_s tiles in BF16 (option precond_bf16): the preconditioner
+    only steers Algorithm 1, so the steps still match the oracle at 1e-8, and the iteration count
+    stays within a few of the FP32 tiles'."""
+    from oracle.monolithic import Discretization, solve_monolithic
+    case = CASES[1]
+    mono = solve_monolithic(case, Discretization(case))
+    its = {}
+    for bf in (0, 1):
+        sol = F.Solver(case)
+        sol.set_option("explicit", 1)
+        sol.set_option("precond_bf16", bf)
+        sol.set_option("ir_eps", 1e-15)
+        sol.assemble()
+        sol.factor()
+        its[bf] = []
+        for n in range(case.n_steps):
+            st = sol.step()
+            its[bf].append(st["iterations"])
+            assert st["true_rel_residual"] <= case.tol
+            assert _rel(sol.get_lambda(), mono[n]["lambda"]) < TOL, (bf, n)
+            for s, (gu, gxi, geta, gp) in enumerate(F.split_fields(case, *sol.get_fields())):
+                u, xi, eta, p = mono[n]["fields"][s]
+                assert np.abs(gu - u).max() < TOL * np.abs(u).max(), (bf, n, s)
+                if eta is not None:
+                    assert np.abs(gp - p).max() < TOL * max(np.abs(p).max(), 1e-300), (bf, n, s)
+        sol.close()
+    assert sum(its[1]) <= 1.25 * sum(its[0]) + 4, its
