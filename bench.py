@@ -288,6 +288,7 @@ def arm_options(args, precision):
         opts = (("explicit", args.fp64_explicit), ("graph", args.graph))
     else:
         opts = (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
+                ("solve_cps", args.cps),
                 ("factor_fp64", args.factor_fp64), ("graph", args.graph), ("factor_nb", args.factor_nb),
                 ("explicit", args.explicit), ("precond_bf16", args.precond_bf16))
     return [(k, v) for k, v in opts if v is not None]
@@ -744,6 +745,7 @@ def main():
     ap.add_argument("--solve-kernel", type=int, default=None, help="1 blocked sweeps, 0 row-step sweeps")
     ap.add_argument("--wpc", type=int, default=None, help="warps per CTA of the local solves")
     ap.add_argument("--chunk", type=int, default=None, help="bytes per shared-memory stage of the solves")
+    ap.add_argument("--cps", type=int, default=None, help="CTAs per SM of the local solves")
     ap.add_argument("--factor-fp64", type=int, default=None, help="mixed: factor in FP64, round to FP32")
     ap.add_argument("--factor-nb", type=int, default=None, help="panel width of the factorisation")
     ap.add_argument("--explicit", type=int, default=1, help="1: explicit local interface operators")

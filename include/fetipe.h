@@ -374,11 +374,12 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *                       bandwidth <= 511.  Mixed precision with "factor_fp64": the Dirichlet
  *                       factor (preconditioner only) this way, the Neumann factor in FP64;
  *                       without "factor_fp64": both.  0: CUDA-core factorisation
- *   "precond_bf16" [0]  mixed precision with "explicit": the Dirichlet preconditioner's S_s
+ *   "precond_bf16" [1]  mixed precision with "explicit": the Dirichlet preconditioner's S_s
  *                       tiles stored in BF16 (half the bytes of the FP32 tiles; products and
  *                       sums stay FP32).  The preconditioner only steers Algorithm 1, so the
- *                       converged result keeps its accuracy; iterations may change.  Takes
- *                       effect at the next fp_factor
+ *                       converged result keeps its accuracy (measured on the large workload: the
+ *                       same iteration counts as FP32 tiles); 0: FP32 tiles.  Takes effect at
+ *                       the next fp_factor
  *   "explicit_2f"  [1]  mixed precision with "explicit" and "factor_fp64": the accurate F applies
  *                       (reference, initial, learned-guess and true residuals) multiply by F_s
  *                       stored as FP32 hi/lo pairs of its upper 32 x 32 tiles (FP32 arithmetic

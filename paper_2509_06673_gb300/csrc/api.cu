@@ -38,6 +38,8 @@ cudaError_t launch_band_mrhs(bool fp32, int bmax, int mt, int grid, cudaStream_t
                              int *counter, void *out, const long long *out_off, int R, int LDp);
 int mrhs_blocks_per_sm(bool fp32, int bmax, int mt, int R, int LDp);
 int mrhs_nr(int b, int mt);
+cudaError_t launch_mrhs_symmetrize(bool fp32, DevTopo D, int S, void *out, const long long *out_off, int mt,
+                                   cudaStream_t st);
 cudaError_t launch_explicit_apply(bool fp32, DevTopo D, int S, int mmax_bnd, const void *ops, const long long *op_off,
                                   double *xloc, const int *fl, cudaStream_t st);
 cudaError_t launch_pack_sym2f(DevTopo D, int S, const double *full, const long long *full_off, float *tiles,
@@ -157,7 +159,7 @@ struct fp_handle {
   double *opF64 = nullptr;              // mixed precision: F_s in FP64 for the accurate applies
   float *opF2 = nullptr;                // ... and as two-float (hi/lo FP32) symmetric tiles
   int explicit_2f = 1;                  // option: accurate mixed-precision F applies from opF2
-  int precond_bf16 = 0;                 // option: mixed precision's S_s tiles in BF16
+  int precond_bf16 = 1;                 // option: mixed precision's S_s tiles in BF16
   int opS_bf16 = 0;                     // the stored S_s tiles are BF16
   const long long *op_off = nullptr, *tile_off = nullptr, *linv_off_dev = nullptr;
   long long op_total = 0, tile_total = 0;
@@ -1128,6 +1130,7 @@ fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, i
     e = launch_band_mrhs(fp32, bmax, mt, grid, h->stream, h->mrhs_s[w], h->mrhs_j0[w], h->mrhs_ntask[w], h->D, fac,
                          linv, h->linv_off_dev, h->csr_val, kind, scratch, sstride, h->counter, out, h->op_off, R,
                          LDp);
+  if (e == cudaSuccess) e = launch_mrhs_symmetrize(fp32, h->D, h->T.S, out, h->op_off, mt, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev[5], h->stream);
   const cudaError_t es = cudaStreamSynchronize(h->stream);
   cudaFree(scratch);

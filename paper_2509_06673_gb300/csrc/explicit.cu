@@ -79,9 +79,16 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     }
     __syncthreads();
     const int nb = (n + 31) / 32;
+    // The tile's right-hand sides vanish above row rs (kind 0: the unit vectors start at b_j0,
+    // the smallest of the tile's dofs, b sorted; kind 1: K's band reaches b_j0 - b), so the
+    // forward sweep starts at block k0.  Only the operator's entries (a, j) with a >= j0 are
+    // formed (the rest by symmetry, k_mrhs_symmetrize): they need the solution at rows >= b_j0
+    // (kind 0) or >= b_j0 - b (kind 1), so the backward sweep stops at the same block k0.
+    const int rs = kind == 0 ? bnd[j0] : max(0, bnd[j0] - b);
+    const int k0 = rs / 32;
     // ---- forward sweep: L y = rhs, z = D^{-1} y into Xs ----
-    int hi = 0;
-    for (int k = 0; k < nb; ++k) {
+    int hi = 32 * k0;
+    for (int k = k0; k < nb; ++k) {
       const int r0 = 32 * k, ncb = min(32, n - r0), rend = min(n, r0 + 32 + b);
       for (int idx = tid; idx < (rend - hi) * MT; idx += blockDim.x) {
         const int r = hi + idx / MT, q = idx % MT;
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       __syncthreads();
     }
     // ---- backward sweep: L^T x = z; x rows kept in the window and written to Xs ----
-    for (int k = nb - 1; k >= 0; --k) {
+    for (int k = nb - 1; k >= k0; --k) {
       const int r0 = 32 * k, ncb = min(32, n - r0), rtop = min(n, r0 + 32 + b);
       for (int idx = tid; idx < ncb * LD; idx += blockDim.x) {
         const int c = idx / LD, sl = idx - c * LD;
@@ -199,15 +206,16 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     // ---- the operator's columns j0 .. j0 + ncol - 1 ----
     T *O = out + out_off[s];
     const int mp = (m + 3) & ~3;  // row stride (padded to 4 for vector loads)
+    const int mlow = m - j0;  // rows a = j0 .. m - 1
     if (kind == 0) {
-      for (int idx = tid; idx < m * ncol; idx += blockDim.x) {
-        const int a = idx / ncol, jj = idx - a * ncol;
+      for (int idx = tid; idx < mlow * ncol; idx += blockDim.x) {
+        const int a = j0 + idx / ncol, jj = idx % ncol;
         O[(long long)a * mp + j0 + jj] = Xs[(long long)bnd[a] * MT + jj];
       }
     } else {
       // S[a][j] = sum_c K[b_a][c] (y_j[c] + [c == b_j]);  y_j vanishes on the rows of b
-      for (int idx = tid; idx < m * ncol; idx += blockDim.x) {
-        const int a = idx / ncol, jj = idx - a * ncol;
+      for (int idx = tid; idx < mlow * ncol; idx += blockDim.x) {
+        const int a = j0 + idx / ncol, jj = idx % ncol;
         const int row = bnd[a], cj = bnd[j0 + jj];
         double acc = 0.0;
         for (int e = cptr[row]; e < cptr[row + 1]; ++e) {
@@ -218,6 +226,20 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       }
     }
     __syncthreads();
+  }
+}
+
+// Completes an operator built by k_band_mrhs (entries (a, j) formed for a >= the first column
+// of j's tile of MT right-hand sides): A[a][j] = A[j][a] for the rest.  One CTA per subdomain.
+template <typename T>
+__global__ void k_mrhs_symmetrize(DevTopo D, T *out, const long long *out_off, int MT) {
+  const int s = blockIdx.x;
+  const DevTpl t = D.tpl[D.sub_tpl[s]];
+  const int m = t.nbnd, mp = (m + 3) & ~3;
+  T *O = out + out_off[s];
+  for (long long idx = threadIdx.x; idx < (long long)m * m; idx += blockDim.x) {
+    const int a = (int)(idx / m), j = (int)(idx % m);
+    if (a < (j / MT) * MT) O[(long long)a * mp + j] = O[(long long)j * mp + a];
   }
 }
 
@@ -564,6 +586,13 @@ static cudaError_t launch_mrhs_T(int grid, cudaStream_t st, const int *ts, const
   if (e != cudaSuccess) return e;
   k_band_mrhs<T, NR, MT><<<grid, 256, smem, st>>>(ts, tj, ntask, D, fac, linv, loff, csr, kind, scratch, sstride,
                                                   counter, out, ooff, R, LDp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mrhs_symmetrize(bool fp32, DevTopo D, int S, void *out, const long long *out_off, int mt,
+                                   cudaStream_t st) {
+  if (fp32) k_mrhs_symmetrize<float><<<S, 256, 0, st>>>(D, (float *)out, out_off, mt);
+  else k_mrhs_symmetrize<double><<<S, 256, 0, st>>>(D, (double *)out, out_off, mt);
   return cudaGetLastError();
 }
 

@@ -117,7 +117,7 @@ __device__ __forceinline__ uint32_t op_off(int r, int k, int rows) {
 }  // namespace
 
 // Shared memory (dynamic): [control 1024 B: mbarrier, tensor-memory address] [B hi, B lo: 128 x 32
-// each] [A hi, A lo: MP x 32 each] [panel: 32 x LD] [d: 32].  MP = 128 ceil(b / 128).
+// each] [A hi, A lo: MP x 32 each] [panel: 32 x (LD + 8)] [d: 32].  MP = 128 ceil(b / 128).
 __global__ void __launch_bounds__(TC_THREADS, 1) k_band_factor_tc(const BandTask *tasks, int ntask, float *base,
                                                                   int MP, int *counter, int *status) {
   extern __shared__ __align__(1024) unsigned char smem_tc[];
@@ -156,15 +156,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_factor_tc(const BandTask
     const BandTask tk = tasks[task];
     float *A = base + tk.fac_off;
     const int n = tk.n, LD = tk.LD, b = tk.b;
-    float *dpan = pan + TC_NB * LD;
+    // panel rows are stored at stride PS = LD + 8 (PS = 8 mod 32): the operand staging below
+    // reads 4 columns x 8 consecutive slots per warp from 32 different banks
+    const int PS = LD + 8;
+    float *dpan = pan + TC_NB * PS;
     for (int J = 0; J < n && !*s_abort; J += TC_NB) {
       const int nbw = min(TC_NB, n - J);
-      for (int e = tid; e < nbw * LD; e += TC_THREADS) pan[e] = A[(long long)J * LD + e];
+      // J and LD are multiples of 32: slot (J + c) mod LD = jl + c for c < 32, and a row r of the
+      // panel's window (J <= r < J + 32 + b) sits in slot jl + (r - J), minus LD once past it
+      const int jl = J % LD;
+      auto slot = [&](int r) { const int v = jl + (r - J); return v >= LD ? v - LD : v; };
+      for (int c = warp; c < nbw; c += TC_THREADS / 32)
+        for (int sl = lane; sl < LD; sl += 32) pan[c * PS + sl] = A[(long long)(J + c) * LD + sl];
       __syncthreads();
       // ---- panel factorisation (CUDA cores) ----
       for (int c = 0; c < nbw; ++c) {
         const int j = J + c;
-        const float d = pan[c * LD + j % LD];
+        float *colc = pan + c * PS;
+        const float d = colc[jl + c];
         const float dinv = 1.0f / d;
         if (tid == 0) {
           dpan[c] = d;
@@ -174,43 +183,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_factor_tc(const BandTask
         // rows of the panel below the pivot: row r updates the panel columns c2 > c whose
         // diagonal lies at or above it (J + c2 <= r)
         for (int r = j + 1 + tid; r <= rmax; r += TC_THREADS) {
-          const int sr = r % LD;
-          const float lrj = pan[c * LD + sr] * dinv;
+          const int sr = slot(r);
+          const float lrj = colc[sr] * dinv;
           const int c2max = min(nbw - 1, r - J);
-          for (int c2 = c + 1; c2 <= c2max; ++c2) pan[c2 * LD + sr] -= lrj * pan[c * LD + (J + c2) % LD];
+          float *pr = pan + (c + 1) * PS + sr;
+          const float *pc = colc + jl + c + 1;
+          for (int c2 = c + 1; c2 <= c2max; ++c2, pr += PS, ++pc) *pr -= lrj * *pc;
         }
         __syncthreads();
-        for (int r = j + 1 + tid; r <= rmax; r += TC_THREADS) pan[c * LD + r % LD] *= dinv;
-        if (tid == 0) pan[c * LD + j % LD] = dinv;
+        for (int r = j + 1 + tid; r <= rmax; r += TC_THREADS) colc[slot(r)] *= dinv;
+        if (tid == 0) colc[jl + c] = dinv;
         __syncthreads();
       }
-      for (int e = tid; e < nbw * LD; e += TC_THREADS) A[(long long)J * LD + e] = pan[e];
+      for (int c = warp; c < nbw; c += TC_THREADS / 32)
+        for (int sl = lane; sl < LD; sl += 32) A[(long long)(J + c) * LD + sl] = pan[c * PS + sl];
       // ---- trailing update of rows / columns [T0, T0 + m) on the tensor cores ----
       const int T0 = J + nbw, m = min(n, J + nbw + b) - T0;
       if (m > 0) {
-        const int MT = (m + 127) >> 7;
-        // A operand: L[T0 + r][J + k] (hi, lo) for r < 128 MT, zero outside the band / panel
+        const int MT = (m + 127) >> 7, RG = 16 * MT;  // 8-row groups of the A operand
+        // A operand: L[T0 + r][J + k] (hi, lo) for r < 128 MT, zero outside the band / panel.
+        // Thread idx writes element (within & 3, within >> 2) of core matrix cm = idx >> 5: a warp
+        // fills one 128-byte core matrix (conflict-free)
         for (int idx = tid; idx < 128 * MT * TC_NB; idx += TC_THREADS) {
-          const int r = idx / TC_NB, k = idx % TC_NB;
+          const int cm = idx >> 5, within = idx & 31;
+          const int r = (cm % RG) * 8 + (within >> 2), k = (cm / RG) * 4 + (within & 3);
           const int row = T0 + r, col = J + k;
           float x = 0.0f;
-          if (r < m && k < nbw && row - col <= b) x = pan[k * LD + row % LD];
+          if (r < m && k < nbw && row - col <= b) x = pan[k * PS + slot(row)];
           const uint32_t h = to_tf32(x);
           const float lo = x - __uint_as_float(h);
-          const uint32_t off = op_off(r, k, 128 * MT);
+          const uint32_t off = (uint32_t)cm * 128 + within * 4;  // = op_off(r, k, 128 MT)
           *reinterpret_cast<uint32_t *>(Ah + off) = h;
           *reinterpret_cast<uint32_t *>(Al + off) = to_tf32(lo);
         }
         for (int nt = 0; nt < MT && !*s_abort; ++nt) {
-          // B operand: d_k L[T0 + 128 nt + r][J + k] (hi, lo)
+          // B operand: d_k L[T0 + 128 nt + r][J + k] (hi, lo), the same conflict-free order
           for (int idx = tid; idx < 128 * TC_NB; idx += TC_THREADS) {
-            const int r = idx / TC_NB, k = idx % TC_NB;
+            const int cm = idx >> 5, within = idx & 31;
+            const int r = (cm % 16) * 8 + (within >> 2), k = (cm / 16) * 4 + (within & 3);
             const int rr = 128 * nt + r, row = T0 + rr, col = J + k;
             float x = 0.0f;
-            if (rr < m && k < nbw && row - col <= b) x = dpan[k] * pan[k * LD + row % LD];
+            if (rr < m && k < nbw && row - col <= b) x = dpan[k] * pan[k * PS + slot(row)];
             const uint32_t h = to_tf32(x);
             const float lo = x - __uint_as_float(h);
-            const uint32_t off = op_off(r, k, 128);
+            const uint32_t off = (uint32_t)cm * 128 + within * 4;  // = op_off(r, k, 128)
             *reinterpret_cast<uint32_t *>(Bh + off) = h;
             *reinterpret_cast<uint32_t *>(Bl + off) = to_tf32(lo);
           }
@@ -292,7 +308,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_factor_tc(const BandTask
 // zero-filled margin so that every operand descriptor's reach stays inside the allocation.
 size_t band_factor_tc_smem(int ldmax, int bmax) {
   const int MP = 128 * ((bmax + 127) / 128);
-  const size_t need = 1024 + 2 * 128 * TC_NB * 4 + 2 * (size_t)MP * TC_NB * 4 + (size_t)TC_NB * ldmax * 4 + TC_NB * 4;
+  const size_t need = 1024 + 2 * 128 * TC_NB * 4 + 2 * (size_t)MP * TC_NB * 4 + (size_t)TC_NB * (ldmax + 8) * 4 +
+                      TC_NB * 4;
   const size_t cap = 227 * 1024;
   return need > cap ? need : std::min(cap, need + 64 * 1024);
 }
