@@ -65,9 +65,19 @@ def config5s():
     return c.with_(perm=W.lognormal_perm(c, sigma=1.0, seed=0))
 
 
+def coarse64():
+    """Profiling case for the coarse projection: a 64 x 64 partition of 2 x 2-cell P1 subdomains
+    (3844 floating subdomains, coarse order 11 532 as in config 5) with small local factors."""
+    from paper_2509_06673_gb300 import workloads as W
+    return W.grid_case("coarse64: 64x64 subdomains of 2x2 P1 cells, nu=0.499 (config 5's coarse order)",
+                       64, 64, 2, 2, order_k=1, lame_lambda=W.lame_from_nu(0.499), tau=1e-3,
+                       precision="mixed", source="manufactured_t")
+
+
 def workload(name, precision=None):
     from paper_2509_06673_gb300 import workloads as W
-    cfg = {"config2": W.config2, "config3": W.config3, "config5": W.config5, "config5s": config5s}[name]()
+    cfg = {"config2": W.config2, "config3": W.config3, "config5": W.config5, "config5s": config5s,
+           "coarse64": coarse64}[name]()
     cfg = cfg.with_(tol=1e-8, max_it=2000)
     if precision:
         cfg = cfg.with_(precision=precision)
@@ -178,13 +188,19 @@ def host_cpu():
     return model, os.cpu_count() or 1
 
 
-# DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum per launch).  The record holds only while the kernel source and its
-# launch shape are the ones captured.
+# DRAM traffic of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum per launch) from
+# one ncu capture on config5s (the same 24 x 24-cell subdomains on a 16 x 16 partition, with config 5's
+# solve launch shape pinned: 8 warps per CTA, 4 KB stages, 2 CTAs per SM): 3.357 GB per full solve
+# against 2.8856 GB algorithmic.  For config 5 it is scaled by the algorithmic bytes (46.416 GB / 2.8856
+# GB: traffic grows with the band bytes, every subdomain being the same size), see
+# profiles/k_band_solve_float_config5s_traffic.md.  A record holds only while the kernel source and
+# the launch shape are the ones captured.
+_BAND_SHA = "14f2dc3e7b85ed1cfc01ae558464fa0c1bc73c0fc89f173be89354b81be1ae27"
 TRAFFIC_RECORDS = [
-    {"workload": "config5", "precision": "mixed", "kernel": "k_band_solve_blk<float>",
-     "shape": [8, 4096, 2], "band_cu_sha256": "14f2dc3e7b85ed1cfc01ae558464fa0c1bc73c0fc89f173be89354b81be1ae27",
-     "bytes_per_launch": 54.394e9 + 0.378e9},
+    {"workload": "config5s", "precision": "mixed", "kernel": "k_band_solve_blk<float>", "shape": [8, 4096, 2],
+     "band_cu_sha256": _BAND_SHA, "bytes_per_launch": 3.3322e9 + 0.0254e9},
+    {"workload": "config5", "precision": "mixed", "kernel": "k_band_solve_blk<float>", "shape": [8, 4096, 2],
+     "band_cu_sha256": _BAND_SHA, "bytes_per_launch": (3.3322e9 + 0.0254e9) * 46.4158e9 / 2.8856e9},
 ]
 
 
@@ -734,7 +750,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--config", default="config5", choices=["config2", "config3", "config4", "config5", "config5s"])
+    ap.add_argument("--config", default="config5",
+                    choices=["config2", "config3", "config4", "config5", "config5s", "coarse64"])
     ap.add_argument("--config4-train", type=int, default=400, help="config4: recorded training steps")
     ap.add_argument("--config4-eval", type=int, default=200, help="config4: evaluation steps")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 comparison arm")

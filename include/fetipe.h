@@ -368,6 +368,10 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *   "stag_window"  [60] a round of Algorithm 1 stops (and restarts from the true residual)
  *                       when its recursive residual has not halved within this many
  *                       iterations; 0 never, 1..100000
+ *   "mlp_tc"       [1]  the learned guess's MLP forward pass (fp_step, fp_mlp_forward) as one
+ *                       fused kernel with the 256 x 256 layer on the tensor cores (tcgen05,
+ *                       bfloat16 operands, FP32 accumulation in tensor memory); 0: the training
+ *                       path's kernels (mma.sync).  Training always uses the latter
  *   "factor_tc"    [1]  FP32 factorisations run on the tensor cores: right-looking panels of 32
  *                       columns, the dense trailing updates as tcgen05 TF32 tiles with the
  *                       3xTF32 split (hi*hi + hi*lo + lo*hi, about FP32 accuracy); half

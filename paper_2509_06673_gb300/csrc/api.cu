@@ -70,6 +70,8 @@ __global__ void k_pack_float_g(DevTopo, double *);
 cudaError_t launch_gemv(const double *H, const double *y, double *alpha, int nH, const int *fl, cudaStream_t st);
 cudaError_t launch_coarse_pack2f(const double *H, int nH, float *tiles, cudaStream_t st);
 size_t band_factor_tc_smem(int ldmax, int bmax);
+cudaError_t launch_mlp_forward_tc(long long rows, const float *X, const float *P, float *out, int num_sms,
+                                  int *status, cudaStream_t st);
 cudaError_t launch_band_factor_tc(const BandTask *tasks, int ntask, float *base, int ldmax, int bmax, int num_sms,
                                   int *counter, int *status, cudaStream_t stream);
 cudaError_t launch_coarse_apply2f(const float *tiles, int nH, const float *ysplit, double *part, double *alpha,
@@ -168,6 +170,7 @@ struct fp_handle {
   double explicit_build_ms = 0;
   int factor_fp64 = 1;     // mixed precision: factor in FP64, round the finished factor to FP32
   int factor_tc = 1;       // FP32 factors on the tensor cores (3xTF32 trailing updates)
+  int mlp_tc = 1;          // MLP inference in the fused tcgen05 kernel
   double *Hband = nullptr, *Hinv = nullptr, *ga = nullptr, *gb = nullptr;
   // mixed precision: (G^T G)^{-1} as hi/lo FP32 upper tiles and the apply's FP64 partials
   float *Htiles = nullptr, *cysplit = nullptr;
@@ -808,6 +811,10 @@ double source_signal(const fp_handle *h, double t) {
 fp_status mlp_forward(fp_handle *h, const float *X, long long rows, float *out) {
   const int CH = fp_handle::CH;
   cudaStream_t s = h->stream;
+  if (h->mlp_tc) {  // one fused launch, the 256 x 256 layer on tcgen05 (mlp_tc.cu)
+    CK(launch_mlp_forward_tc(rows, X, h->mlpP, out, h->num_sms, h->status, s));
+    return FP_OK;
+  }
   for (long long r0 = 0; r0 < rows; r0 += CH) {
     const int m = (int)std::min<long long>(CH, rows - r0);
     k_mlp_l1<<<(m * MLP_NH + 255) / 256, 256, 0, s>>>(m, X + r0 * MLP_NIN, h->mlpP, nullptr, h->h1);
@@ -2299,6 +2306,7 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "explicit") { if (v < 0 || v > 1) return bad(); h->explicit_ops = v; }
   else if (k == "explicit_tile") { if (v != 0 && v != 16 && v != 32) return bad(); h->explicit_tile = v; }
   else if (k == "autotune") { if (v < 0 || v > 1) return bad(); h->autotune = v; }
+  else if (k == "mlp_tc") { if (v < 0 || v > 1) return bad(); h->mlp_tc = v; }
   else if (k == "factor_tc") { if (v < 0 || v > 1) return bad(); h->factor_tc = v; }
   else if (k == "precond_bf16") { if (v < 0 || v > 1) return bad(); h->precond_bf16 = v; }
   else if (k == "explicit_2f") { if (v < 0 || v > 1) return bad(); h->explicit_2f = v; }

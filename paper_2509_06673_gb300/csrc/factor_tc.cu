@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include "device.cuh"
+#include "tcgen05.cuh"
 
 namespace fp {
 namespace {
@@ -36,83 +37,23 @@ namespace {
 constexpr int TC_NB = 32;          // panel width = K of the trailing update
 constexpr int TC_THREADS = 256;    // 8 warps
 constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t IDESC_TF32_128x128 = tc::idesc_f32acc(2u, 128u, 128u);  // kind::tf32, M = N = 128
 
-__device__ __forceinline__ uint32_t s_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+using tc::fence_after;
+using tc::fence_before;
+using tc::mbar_init1;
+using tc::mbar_wait_bounded;
+using tc::proxy_fence;
+using tc::s_addr;
+using tc::smem_desc;
+using tc::tmem_ld32;
+using tc::to_tf32;
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t accum) {
+  tc::mma_tf32(d, a, b, IDESC_TF32_128x128, accum);
 }
-__device__ __forceinline__ void mbar_init1(uint64_t *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(s_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait (about 2^31 SM cycles)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > (1LL << 31)) return false;
-  }
-  return true;
-}
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
-  return d;                // base offset 0, layout type 0 (no swizzle)
-}
-// instruction descriptor: kind::tf32, D FP32, A and B TF32, both K-major, M = 128, N = 128
-constexpr uint32_t IDESC_TF32_128x128 =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC_TF32_128x128), "r"(accum)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 32 consecutive FP32 accumulator columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// byte offset of element (r, k) in a K-major no-swizzle operand of `rows` rows
-__device__ __forceinline__ uint32_t op_off(int r, int k, int rows) {
-  return (uint32_t)((k >> 2) * rows * 16 + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) { tc::mma_commit(bar); }
+__device__ __forceinline__ void tc_fence_before() { fence_before(); }
+__device__ __forceinline__ void tc_fence_after() { fence_after(); }
 
 }  // namespace
 
@@ -212,7 +153,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_factor_tc(const BandTask
           if (r < m && k < nbw && row - col <= b) x = pan[k * PS + slot(row)];
           const uint32_t h = to_tf32(x);
           const float lo = x - __uint_as_float(h);
-          const uint32_t off = (uint32_t)cm * 128 + within * 4;  // = op_off(r, k, 128 MT)
+          const uint32_t off = (uint32_t)cm * 128 + within * 4;  // the offset of (r, k) in the layout above
           *reinterpret_cast<uint32_t *>(Ah + off) = h;
           *reinterpret_cast<uint32_t *>(Al + off) = to_tf32(lo);
         }
@@ -226,7 +167,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_factor_tc(const BandTask
             if (rr < m && k < nbw && row - col <= b) x = dpan[k] * pan[k * PS + slot(row)];
             const uint32_t h = to_tf32(x);
             const float lo = x - __uint_as_float(h);
-            const uint32_t off = (uint32_t)cm * 128 + within * 4;  // = op_off(r, k, 128)
+            const uint32_t off = (uint32_t)cm * 128 + within * 4;  // the offset of (r, k) in the layout above
             *reinterpret_cast<uint32_t *>(Bh + off) = h;
             *reinterpret_cast<uint32_t *>(Bl + off) = to_tf32(lo);
           }
