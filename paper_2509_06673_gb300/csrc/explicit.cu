@@ -299,6 +299,17 @@ __device__ __forceinline__ void store_tile_elem(float *p, float v) { *p = v; }
 __device__ __forceinline__ void store_tile_elem(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ float load_tile_elem(const float *p) { return *p; }
 __device__ __forceinline__ float load_tile_elem(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+// two adjacent elements (p even-aligned)
+__device__ __forceinline__ void load_tile_pair(const float *p, float &a, float &b) {
+  const float2 v = *reinterpret_cast<const float2 *>(p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void load_tile_pair(const __nv_bfloat16 *p, float &a, float &b) {
+  const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+  a = v.x;
+  b = v.y;
+}
 
 template <typename Tin, typename Tout>
 __global__ void k_pack_sym(DevTopo D, const Tin *full, const long long *full_off, Tout *tiles,
@@ -317,12 +328,13 @@ __global__ void k_pack_sym(DevTopo D, const Tin *full, const long long *full_off
 }
 
 // y_b = A_s x_b for the tiled symmetric A_s, in place on the local vectors at the rows b_s.
-// Warp w takes tiles w, w + 8, ...; lane c holds column c of a tile (one coalesced 128-byte
-// row per load).  An off-diagonal tile gives A_IJ^T x_I to y_J (a per-lane sum) and A_IJ x_J
-// to y_I: the 32 row sums come out of a transposing butterfly (at offset k a lane keeps the
-// half of its values selected by bit k of its lane index and adds the partner's copy of that
-// half: 31 shuffles, and lane l ends with row sum l).  Partial sums land in shared memory and
-// are added in a fixed order.
+// Warp w takes tiles w, w + 8, ...; a lane holds a pair of adjacent columns of every other row
+// (16 loads of two whole rows per warp and tile).  An off-diagonal tile gives A_IJ^T x_I to y_J
+// (per-lane column sums, the two row parities added across the half-warps) and A_IJ x_J to y_I:
+// the 32 row sums come out of a transposing butterfly within each half-warp (at offset k a lane
+// keeps the half of its values selected by bit k of its column-pair index and adds the
+// partner's copy of that half: 15 shuffles).  Partial sums land in shared memory and are added
+// in a fixed order.
 // With vlam given, x_b is formed here from the multiplier vector (x_b = B_s^T vlam, the fixed
 // dofs of a floating subdomain zero when skip_fixed), as k_scatter would, instead of being read
 // from the local vector: one launch and one pass over the rows b_s fewer per apply.
@@ -364,33 +376,47 @@ __global__ void __launch_bounds__(256) k_explicit_apply_sym(DevTopo D, const TS 
   __syncthreads();
   const TS *A = tiles + tile_off[s];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // lane (h, c) = (lane >> 4, lane & 15) holds columns 2c, 2c + 1 of the rows 2i + h (i < 16): one
+  // load instruction brings two whole rows (coalesced), 16 per tile
+  const int h = lane >> 4, c = lane & 15;
   for (int tile = warp; tile < ntile; tile += nw) {
     int I, J;
     tile_ij(tile, nt, I, J);
     const TS *T = A + (long long)tile * 1024;
-    float v[32];
+    float v0[16], v1[16];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = load_tile_elem(T + r * 32 + lane);
-    if (I < J) {
-      float acc = 0.0f;
+    for (int i = 0; i < 16; ++i) load_tile_pair(T + (2 * i + h) * 32 + 2 * c, v0[i], v1[i]);
+    if (I < J) {  // A_IJ^T x_I: column sums, the two row parities added across the half-warps
+      float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-      for (int r = 0; r < 32; ++r) acc += v[r] * xs[32 * I + r];
-      cp[tile * 32 + lane] = acc;
-    }
-    const float xj = xs[32 * J + lane];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] *= xj;
-#pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
-      const bool up = (lane & k) != 0;
-#pragma unroll
-      for (int i = 0; i < k; ++i) {
-        const float send = up ? v[i] : v[i + k];
-        const float keep = up ? v[i + k] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, k);
+      for (int i = 0; i < 16; ++i) {
+        const float xr = xs[32 * I + 2 * i + h];
+        a0 += v0[i] * xr;
+        a1 += v1[i] * xr;
+      }
+      a0 += __shfl_xor_sync(FULL, a0, 16);
+      a1 += __shfl_xor_sync(FULL, a1, 16);
+      if (h == 0) {
+        cp[tile * 32 + 2 * c] = a0;
+        cp[tile * 32 + 2 * c + 1] = a1;
       }
     }
-    rp[tile * 32 + lane] = v[0];
+    // A_IJ x_J: the lane's part of row 2i + h, then a transposing butterfly over the 16 lanes of
+    // the half-warp (offsets 8, 4, 2, 1): lane (h, c) ends with the sum of row 2c + h
+    const float xj0 = xs[32 * J + 2 * c], xj1 = xs[32 * J + 2 * c + 1];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v0[i] = v0[i] * xj0 + v1[i] * xj1;
+#pragma unroll
+    for (int k = 8; k >= 1; k >>= 1) {
+      const bool up = (c & k) != 0;
+#pragma unroll
+      for (int i = 0; i < k; ++i) {
+        const float send = up ? v0[i] : v0[i + k];
+        const float keep = up ? v0[i + k] : v0[i];
+        v0[i] = keep + __shfl_xor_sync(FULL, send, k);
+      }
+    }
+    rp[tile * 32 + 2 * c + h] = v0[0];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
