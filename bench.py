@@ -190,17 +190,17 @@ def host_cpu():
 
 # DRAM traffic of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum per launch) from
 # one ncu capture on config5s (the same 24 x 24-cell subdomains on a 16 x 16 partition, with config 5's
-# solve launch shape pinned: 8 warps per CTA, 4 KB stages, 2 CTAs per SM): 3.357 GB per full solve
+# solve launch shape pinned: 8 warps per CTA, 4 KB stages, 2 CTAs per SM): 2.983 GB per full solve
 # against 2.8856 GB algorithmic.  For config 5 it is scaled by the algorithmic bytes (46.416 GB / 2.8856
 # GB: traffic grows with the band bytes, every subdomain being the same size), see
 # profiles/k_band_solve_float_config5s_traffic.md.  A record holds only while the kernel source and
 # the launch shape are the ones captured.
-_BAND_SHA = "14f2dc3e7b85ed1cfc01ae558464fa0c1bc73c0fc89f173be89354b81be1ae27"
+_BAND_SHA = "72822810c8358dfaa022303edd053542db6450e24bee1ecd91371ee3a6c68c40"
 TRAFFIC_RECORDS = [
     {"workload": "config5s", "precision": "mixed", "kernel": "k_band_solve_blk<float>", "shape": [8, 4096, 2],
-     "band_cu_sha256": _BAND_SHA, "bytes_per_launch": 3.3322e9 + 0.0254e9},
+     "band_cu_sha256": _BAND_SHA, "bytes_per_launch": 2.9578e9 + 0.0256e9},
     {"workload": "config5", "precision": "mixed", "kernel": "k_band_solve_blk<float>", "shape": [8, 4096, 2],
-     "band_cu_sha256": _BAND_SHA, "bytes_per_launch": (3.3322e9 + 0.0254e9) * 46.4158e9 / 2.8856e9},
+     "band_cu_sha256": _BAND_SHA, "bytes_per_launch": (2.9578e9 + 0.0256e9) * 46.4158e9 / 2.8856e9},
 ]
 
 

@@ -442,6 +442,9 @@ typedef struct {
   /* device time of the FP32 factorisations on the tensor cores ("factor_tc"; index 0 Neumann,
    * 1 Dirichlet), milliseconds; 0 where that factor was not computed this way */
   double factor_tc_ms[2];
+  /* device time of each explicit operator's multi-right-hand-side build (index 0 F_s, 1 S_s;
+   * the parts of explicit_ms), milliseconds; 0 where not built */
+  double mrhs_ms[2];
 } fp_tuning;
 fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out);
 

@@ -26,8 +26,8 @@ cudaError_t launch_band_factor(bool fp32, const BandTask *tasks, int ntask, void
 cudaError_t launch_band_solve(bool fp32, int mmax, int grid, int wpc, cudaStream_t stream, const BandTask *tasks,
                               int ntask, const void *fac, double *x, int *counter, int *status, const int *done);
 cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int chunk, cudaStream_t stream,
-                                  const BandTask *tasks, int ntask, const void *fac, const void *linv, double *x,
-                                  int *counter, int *status, const int *done);
+                                  const BandTask *tasks, int ntask, const void *fac, double *x, int *counter,
+                                  int *status, const int *done);
 cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
                              cudaStream_t stream);
 cudaError_t launch_round_to_float(const double *src, float *dst, long long n, cudaStream_t stream);
@@ -141,9 +141,8 @@ struct fp_handle {
   double *csr_val = nullptr, *fstat = nullptr, *Zn = nullptr, *E0n = nullptr, *Reta = nullptr;
   double *sell_val = nullptr;  // sliced ELL copy of the Neumann matrices (FP64 residuals)
   void *facN = nullptr, *facD = nullptr, *linvN = nullptr, *linvD = nullptr;
-  double *linvH = nullptr;
   long long linv_total = 0;
-  int solve_kernel = 1;    // 1: blocked sweeps with inverse diagonal blocks, 0: row-step sweeps
+  int solve_kernel = 1;    // 1: blocked sweeps (32-column blocks streamed by TMA), 0: row-step sweeps
   int solve_wpc = 0;       // warps per CTA of the solve kernels (0: autotuned / from the task count)
   int solve_chunk = 0;     // bytes per ring stage of the blocked solve (0: autotuned / 8192)
   int solve_cps = 0;       // CTAs per SM of the blocked solve (0: autotuned / 1)
@@ -533,11 +532,10 @@ fp_status build_device(fp_handle *h) {
 
 // ------------------------------ building blocks -------------------------------------
 // The blocked solve's launch shape made legal for the element size: a stage holds at least
-// one inverse block and one column of the widest band; the ring fits the shared memory of
-// one CTA (and of cps CTAs per SM).
+// one column of the widest band; the ring fits the shared memory of one CTA (and of cps CTAs
+// per SM).
 fp_handle::SolveShape legal_shape(const fp_handle *h, fp_handle::SolveShape sh, bool fp32) {
   const int esz = fp32 ? 4 : 8;
-  sh.chunk = std::max(sh.chunk, 1024 * esz);
   sh.chunk = std::max(sh.chunk, (std::max(h->ldmax, h->T.LDH) * esz + 1023) / 1024 * 1024);
   while (sh.wpc > 1 && (size_t)sh.wpc * 3 * (sh.chunk + 8) > 200 * 1024) sh.wpc >>= 1;
   if (sh.cps < 1) sh.cps = 1;
@@ -557,12 +555,12 @@ fp_handle::SolveShape default_shape(const fp_handle *h, int ntask) {
 }
 
 fp_status launch_solve_shaped(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac,
-                              const void *linv, double *x, int mmax, const int *done, fp_handle::SolveShape sh) {
+                              double *x, int mmax, const int *done, fp_handle::SolveShape sh) {
   CK(cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream));
-  if (h->solve_kernel == 1 && linv) {
+  if (h->solve_kernel == 1) {
     sh = legal_shape(h, sh, fp32);
     const int grid = std::max(1, std::min(sh.cps * h->num_sms, (ntask + sh.wpc - 1) / sh.wpc));
-    CK(launch_band_solve_blk(fp32, mmax, grid, sh.wpc, sh.chunk, h->stream, tasks, ntask, fac, linv, x, h->counter,
+    CK(launch_band_solve_blk(fp32, mmax, grid, sh.wpc, sh.chunk, h->stream, tasks, ntask, fac, x, h->counter,
                              h->status, done));
   } else {
     int wpc = ntask >= 4 * h->num_sms ? 4 : (ntask >= 2 * h->num_sms ? 2 : 1);
@@ -573,10 +571,10 @@ fp_status launch_solve_shaped(fp_handle *h, bool fp32, const BandTask *tasks, in
   return FP_OK;
 }
 
-fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac, const void *linv,
-                       double *x, int mmax, const int *done) {
+fp_status launch_solve(fp_handle *h, bool fp32, const BandTask *tasks, int ntask, const void *fac, double *x,
+                       int mmax, const int *done) {
   const fp_handle::SolveShape sh = h->shape.wpc > 0 ? h->shape : default_shape(h, ntask);
-  return launch_solve_shaped(h, fp32, tasks, ntask, fac, linv, x, mmax, done, sh);
+  return launch_solve_shaped(h, fp32, tasks, ntask, fac, x, mmax, done, sh);
 }
 
 fp_status next_event(fp_handle *h, cudaEvent_t *e) {
@@ -606,8 +604,7 @@ fp_status solve_local(fp_handle *h, bool dirichlet, double *x, const int *done) 
     TRY(next_event(h, &e1));
     CK(cudaEventRecordWithFlags(e0, h->stream, evflags));
   }
-  const void *linv = dirichlet ? h->linvD : h->linvN;
-  TRY(launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, linv, x, h->mmax, done));
+  TRY(launch_solve(h, h->P.precision == FP_PREC_MIXED, tasks, h->ntask, fac, x, h->mmax, done));
   if (timed) {
     CK(cudaEventRecordWithFlags(e1, h->stream, evflags));
     (h->capturing ? h->gpending : h->pending).push_back({dirichlet ? 1 : 0, e0, e1});
@@ -648,7 +645,7 @@ fp_status solve_refined(fp_handle *h, const double *b, double *x, int sweeps, co
     TRY(solve_local(h, false, h->XR, skip));
     k_local_add<<<1184, 256, 0, h->stream>>>(x, h->XR, nv, skip);
     const double eps = h->ir_eps > 0 ? h->ir_eps : std::min(1e-10, std::max(1e-15, 1e-2 * h->P.tol));
-    k_ir_check<<<RED_BLOCKS, 256, 0, h->stream>>>(x, h->XR, nv, eps * eps, h->partial,
+    k_ir_check<<<RED_BLOCKS_IR, 256, 0, h->stream>>>(x, h->XR, nv, eps * eps, h->partial,
                                                   h->red_counter + 2, h->fl_ir, h->ir_prev,
                                                   h->ir_stag * h->ir_stag, h->ir_prev + 1);
     CKL();
@@ -994,7 +991,6 @@ fp_status factor_coarse(fp_handle *h) {
   if (!h->Hband) {
     TRY(dalloc(h, &h->Hband, (size_t)T.nH * T.LDH));
     TRY(dalloc(h, &h->Hinv, (size_t)T.nH * T.nH));
-    TRY(dalloc(h, &h->linvH, 1024 * (size_t)((T.nH + 31) / 32)));
   }
   k_coarse_G<<<(T.n_lambda + 255) / 256, 256, 0, h->stream>>>(h->D, h->ga, h->gb);
   k_pack_float_g<<<(T.NF + 7) / 8, 256, 0, h->stream>>>(h->D, const_cast<double *>(h->D.float_g));
@@ -1007,8 +1003,7 @@ fp_status factor_coarse(fp_handle *h) {
   CK(launch_band_factor(false, h->taskH, 1, h->Hband, NB, h->status, smem, h->stream));
   k_identity<<<1024, 256, 0, h->stream>>>(h->Hinv, T.nH);
   CKL();
-  CK(launch_band_linv(false, h->taskH, 1, h->Hband, h->linvH, h->stream));
-  TRY(launch_solve(h, false, h->tasksHinv, T.nH, h->Hband, h->linvH, h->Hinv, h->mmaxH, nullptr));
+  TRY(launch_solve(h, false, h->tasksHinv, T.nH, h->Hband, h->Hinv, h->mmaxH, nullptr));
   if (h->P.precision == FP_PREC_MIXED && h->coarse_2f) {
     const long long nt = (T.nH + 31) / 32, ntile = nt * (nt + 1) / 2;
     if (!h->Htiles) {
@@ -1088,7 +1083,7 @@ fp_status autotune_solve(fp_handle *h) {
       for (int rep = 0; rep < 3; ++rep) {
         CK(cudaMemsetAsync(h->XB, 0, nv * sizeof(double), h->stream));
         CK(cudaEventRecord(e0, h->stream));
-        TRY(launch_solve_shaped(h, fp32, h->tasksN, h->ntask, h->facN, h->linvN, h->XB, h->mmax, nullptr, sh));
+        TRY(launch_solve_shaped(h, fp32, h->tasksN, h->ntask, h->facN, h->XB, h->mmax, nullptr, sh));
         CK(cudaEventRecord(e1, h->stream));
         CK(cudaEventSynchronize(e1));
         float ms = 0;
@@ -1146,6 +1141,7 @@ fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, i
   float ms = 0;
   cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]);
   h->tuning.explicit_ms += ms;
+  h->tuning.mrhs_ms[kind] += ms;
   return FP_OK;
 }
 
@@ -1770,7 +1766,10 @@ fp_status fp_factor(fp_handle *h) {
   h->tuning.explicit_ms = 0;
   h->tuning.solve_mmax = h->mmax;
   h->tuning.factor_tc_ms[0] = h->tuning.factor_tc_ms[1] = 0.0;
-  for (int k = 0; k < 2; ++k) h->tuning.mrhs_nr[k] = h->tuning.mrhs_mt[k] = h->tuning.mrhs_esz[k] = 0;
+  for (int k = 0; k < 2; ++k) {
+    h->tuning.mrhs_nr[k] = h->tuning.mrhs_mt[k] = h->tuning.mrhs_esz[k] = 0;
+    h->tuning.mrhs_ms[k] = 0.0;
+  }
   CK(cudaMemsetAsync(h->ir_prev, 0, 2 * sizeof(double), h->stream));
   TRY(h->P.precision == FP_PREC_MIXED ? factor_T<float>(h) : factor_T<double>(h));
   TRY(factor_coarse(h));

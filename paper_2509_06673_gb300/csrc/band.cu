@@ -372,7 +372,8 @@ FP_SOLVE_INST(float, 12)
 FP_SOLVE_INST(float, 16)
 
 // ============================ blocked sweeps ===========================================
-// Inverse of every unit-lower 32 x 32 diagonal block of L, in FP64 from the stored factor,
+// Inverse of every unit-lower 32 x 32 diagonal block of L (used by the explicit operator build,
+// whose multi-right-hand-side sweeps apply them as 32 x 32 products), in FP64 from the stored factor,
 // stored row-major (Linv[r][c], zero above the diagonal; identity beyond row n - 1 of a
 // partial last block).  One CTA per task, one warp per block, lane c computes column c by
 // forward substitution x_r = [r == c] - sum_{k<r} L[r][k] x_k.
@@ -406,14 +407,14 @@ __global__ void k_band_linv(const BandTask *tasks, int ntask, const T *fbase, T 
   }
 }
 
-// Per-warp request stream of the blocked solve: forward [Linv_q, column chunks of block q],
-// backward [column chunks of block q (descending), Linv_q].  Request q of the warp lives in
+// Per-warp request stream of the blocked solve: the column chunks of block q, forward in
+// ascending order, backward in descending order.  Request q of the warp lives in
 // ring stage q % SOLVE_STAGES and completes phase (q / SOLVE_STAGES) & 1 of its mbarrier.
 template <typename T>
 struct BlkStream {
   unsigned char *ring;
   uint64_t *bar;
-  const T *fac, *linv;
+  const T *fac;
   int chunk;                 // bytes per ring stage
   int n, LD, C, nblk, total;
   uint32_t seq, issued, seq_task;
@@ -422,25 +423,18 @@ struct BlkStream {
   __device__ __forceinline__ int cpb(int q) const { return (min(32, n - 32 * q) + C - 1) / C; }
   __device__ __forceinline__ void issue_one() {
     const int st = issued % SOLVE_STAGES;
-    const void *src;
-    uint32_t bytes;
-    if (ik < 0) {
-      src = linv + (long long)iq * 1024;
-      bytes = 1024 * sizeof(T);
-    } else {
-      const int c0 = 32 * iq + ik * C;
-      src = fac + (long long)c0 * LD;
-      bytes = (uint32_t)min(C, n - c0) * LD * sizeof(T);
-    }
+    const int c0 = 32 * iq + ik * C;
+    const void *src = fac + (long long)c0 * LD;
+    const uint32_t bytes = (uint32_t)min(C, n - c0) * LD * sizeof(T);
     mbar_expect_tx(&bar[st], bytes);
     bulk_g2s(ring + (size_t)st * chunk, src, bytes, &bar[st]);
     ++issued;
     if (idir == 0) {
       if (ik + 1 < cpb(iq)) ++ik;
-      else if (iq + 1 < nblk) { ++iq; ik = -1; }
+      else if (iq + 1 < nblk) { ++iq; ik = 0; }
       else { idir = 1; iq = nblk - 1; ik = cpb(iq) - 1; }
     } else {
-      if (ik >= 0) --ik;
+      if (ik > 0) --ik;
       else if (iq > 0) { --iq; ik = cpb(iq) - 1; }
       else idir = 2;
     }
@@ -463,10 +457,15 @@ struct BlkStream {
   }
 };
 
+// Blocked sweeps of L D L^T x = b, one warp per system from the work queue.  The window of
+// pending rows stays in registers by slot (lane l, register m: slot group (q + m) mod M of block
+// q), and the factor streams through the warp's ring in chunks of C columns, each byte read once
+// per sweep.  The 32 columns of a block are applied one by one: the forward sweep in axpy form
+// (one shuffle per column), the backward sweep in dot form (one warp reduction per column).
 template <typename T, int MMAX>
 __global__ void __launch_bounds__(256, 1) k_band_solve_blk(const BandTask *tasks, int ntask, const T *fbase,
-                                                        const T *lbase, double *xbase, int *counter, int *status,
-                                                        const int *done, int chunk) {
+                                                        double *xbase, int *counter, int *status, const int *done,
+                                                        int chunk) {
   if (done && *done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -488,7 +487,6 @@ __global__ void __launch_bounds__(256, 1) k_band_solve_blk(const BandTask *tasks
     if (task >= ntask) break;
     const BandTask tk = tasks[task];
     S.fac = fbase + tk.fac_off;
-    S.linv = lbase + tk.linv_off;
     double *x = xbase + tk.x_off;
     const int n = tk.n, LD = tk.LD, M = LD / 32;
     int C = 32;
@@ -496,10 +494,9 @@ __global__ void __launch_bounds__(256, 1) k_band_solve_blk(const BandTask *tasks
     const int nblk = (n + 31) / 32;
     S.n = n; S.LD = LD; S.C = C; S.nblk = nblk;
     S.total = 0;
-    for (int q = 0; q < nblk; ++q) S.total += 1 + S.cpb(q);
-    S.total *= 2;
+    for (int q = 0; q < nblk; ++q) S.total += 2 * S.cpb(q);
     S.seq_task = S.seq;
-    S.idir = 0; S.iq = 0; S.ik = -1;
+    S.idir = 0; S.iq = 0; S.ik = 0;
     S.top_up(lane);
     // ------------------------------- forward ------------------------------------
     T w[MMAX];
@@ -515,20 +512,11 @@ __global__ void __launch_bounds__(256, 1) k_band_solve_blk(const BandTask *tasks
       for (int m = 0; m < MMAX; ++m) offs[m] = (m < M) ? ((g + m) % M) * 32 + lane : 0;
       const int rr = j0 + LD + lane;
       const T refill = rr < n ? T(x[rr]) : T(0);
-      // y_J = Linv_q w_J (rotated order: conflict-free shared-memory reads)
-      const T *Ls = S.acquire();
-      if (S.abort) break;
-      T y0 = T(0), y1 = T(0);
-#pragma unroll 4
-      for (int i = 0; i < 32; i += 2) {
-        const int k0 = (lane + i) & 31, k1 = (lane + i + 1) & 31;
-        y0 += Ls[lane * 32 + k0] * __shfl_sync(FULL, w[0], k0);
-        y1 += Ls[lane * 32 + k1] * __shfl_sync(FULL, w[0], k1);
-      }
-      const T y = y0 + y1;
-      S.release(lane);
-      // rank-32 update of the window with the block's columns
-      T zout = T(0), corr0 = T(0);
+      // column by column (axpy form): y_cc is lane cc's pending value once the columns before
+      // it are applied.  Column cc's slot of lane l in the first slot group holds L[j0 + l][j0 + cc]
+      // for l > cc (the in-block part), 1/d for l == cc, and the row j0 + LD + l of the next
+      // window for l < cc; the other slot groups hold the rows of the window.
+      T wq = w[0], zout = T(0), corr0 = T(0);
       const int ncol = min(32, n - j0);
       for (int c0c = 0; c0c < ncol && !S.abort; c0c += C) {
         if (c0c) S.release(lane);
@@ -538,10 +526,11 @@ __global__ void __launch_bounds__(256, 1) k_band_solve_blk(const BandTask *tasks
 #pragma unroll 2
         for (int cc = c0c; cc < cend; ++cc) {
           const T *col = cb + (size_t)(cc - c0c) * LD;
-          const T yc = __shfl_sync(FULL, y, cc);
           const T c0 = col[offs[0]];
-          if (lane == cc) zout = y * c0;
-          if (lane < cc) corr0 += c0 * yc;
+          const T yc = __shfl_sync(FULL, wq, cc);
+          if (lane > cc) wq -= c0 * yc;
+          else if (lane == cc) zout = yc * c0;
+          else corr0 += c0 * yc;
 #pragma unroll
           for (int m = 1; m < MMAX; ++m)
             if (m < M) w[m] -= col[offs[m]] * yc;
@@ -569,36 +558,26 @@ __global__ void __launch_bounds__(256, 1) k_band_solve_blk(const BandTask *tasks
       for (int m = 0; m < MMAX; ++m) offs[m] = (m < M) ? ((g + m) % M) * 32 + lane : 0;
       const T zin = (j0 + lane < n) ? T(x[j0 + lane]) : T(0);
       const int ncol = min(32, n - j0);
-      T own = T(0);   // lane c ends with sum_{r > j0 + 31} L[r][j0 + c] x_r
-      // chunks in descending order (the request stream), columns in any order inside one
+      // columns in descending order (dot form): x_cc = z_cc - sum_{r > cc} L[r][j0 + cc] x_r, the
+      // rows of the block below cc (x of lanes > cc, final by then) and of the window
+      T xc = T(0);
       for (int kc = (ncol - 1) / C; kc >= 0 && !S.abort; --kc) {
         if (kc != (ncol - 1) / C) S.release(lane);
         const T *cb = S.acquire();
         if (S.abort) break;
         const int c0c = kc * C, cend = min(ncol, c0c + C);
 #pragma unroll 4
-        for (int cc = c0c; cc < cend; ++cc) {
+        for (int cc = cend - 1; cc >= c0c; --cc) {
           const T *col = cb + (size_t)(cc - c0c) * LD;
-          T sacc = (lane < cc) ? col[offs[0]] * xw[0] : T(0);
+          T sacc = col[offs[0]] * (lane < cc ? xw[0] : (lane > cc ? xc : T(0)));
 #pragma unroll
           for (int m = 1; m < MMAX; ++m)
             if (m < M) sacc += col[offs[m]] * xw[m];
           sacc = warp_sum(sacc);
-          if (lane == cc) own = sacc;
+          if (lane == cc) xc = zin - sacc;
         }
       }
       if (S.abort) break;
-      S.release(lane);
-      const T t = zin - own;
-      const T *Ls = S.acquire();
-      if (S.abort) break;
-      T xc0 = T(0), xc1 = T(0);
-#pragma unroll 4
-      for (int i = 0; i < 32; i += 2) {
-        xc0 += Ls[i * 32 + lane] * __shfl_sync(FULL, t, i);
-        xc1 += Ls[(i + 1) * 32 + lane] * __shfl_sync(FULL, t, i + 1);
-      }
-      const T xc = xc0 + xc1;
       S.release(lane);
       xw[0] = xc;
       if (j0 + lane < n) x[j0 + lane] = double(xc);
@@ -657,9 +636,9 @@ static cudaError_t launch_solve_T(int mmax, int grid, int wpc, cudaStream_t stre
 
 template <typename T>
 static cudaError_t launch_solve_blk_T(int mmax, int grid, int wpc, int chunk, cudaStream_t stream,
-                                      const BandTask *tasks, int ntask, const T *fac, const T *linv, double *x,
-                                      int *counter, int *status, const int *done) {
-  void (*kern)(const BandTask *, int, const T *, const T *, double *, int *, int *, const int *, int) = nullptr;
+                                      const BandTask *tasks, int ntask, const T *fac, double *x, int *counter,
+                                      int *status, const int *done) {
+  void (*kern)(const BandTask *, int, const T *, double *, int *, int *, const int *, int) = nullptr;
   switch (mmax) {
     case 4: kern = k_band_solve_blk<T, 4>; break;
     case 8: kern = k_band_solve_blk<T, 8>; break;
@@ -669,20 +648,19 @@ static cudaError_t launch_solve_blk_T(int mmax, int grid, int wpc, int chunk, cu
   const size_t smem = (size_t)wpc * SOLVE_STAGES * (chunk + 8);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 32 * wpc, smem, stream>>>(tasks, ntask, fac, linv, x, counter, status, done, chunk);
+  kern<<<grid, 32 * wpc, smem, stream>>>(tasks, ntask, fac, x, counter, status, done, chunk);
   return cudaGetLastError();
 }
 
-// chunk: bytes per ring stage (multiple of 1024, >= 1024 * sizeof(T) to hold an inverse
-// block and >= one factor column), wpc: warps per CTA (1..8).
+// chunk: bytes per ring stage (multiple of 1024, >= one factor column), wpc: warps per CTA (1..8).
 cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int chunk, cudaStream_t stream,
-                                  const BandTask *tasks, int ntask, const void *fac, const void *linv, double *x,
-                                  int *counter, int *status, const int *done) {
+                                  const BandTask *tasks, int ntask, const void *fac, double *x, int *counter,
+                                  int *status, const int *done) {
   if (fp32)
-    return launch_solve_blk_T<float>(mmax, grid, wpc, chunk, stream, tasks, ntask, (const float *)fac,
-                                     (const float *)linv, x, counter, status, done);
-  return launch_solve_blk_T<double>(mmax, grid, wpc, chunk, stream, tasks, ntask, (const double *)fac,
-                                    (const double *)linv, x, counter, status, done);
+    return launch_solve_blk_T<float>(mmax, grid, wpc, chunk, stream, tasks, ntask, (const float *)fac, x, counter,
+                                     status, done);
+  return launch_solve_blk_T<double>(mmax, grid, wpc, chunk, stream, tasks, ntask, (const double *)fac, x, counter,
+                                    status, done);
 }
 
 __global__ void k_round_to_float(const double *src, float *dst, long long n) {

@@ -110,7 +110,11 @@ enum FlSlot { FL_DONE = 0, FL_ITER, FL_STATUS, FL_MAXIT, FL_IRSKIP, FL_IRSWEEPS,
 // step): time t_n, extrapolation ratio rho of the source signal, squared tolerance
 enum StepSlot { ST_T = 0, ST_RHO, ST_TOL2, ST_N = 4 };
 enum RedOp { OP_STORE = 0, OP_PQ = 1, OP_RZ_INIT = 2, OP_RZ = 3, OP_RNORM = 4, OP_RNORM0 = 5 };
-constexpr int RED_BLOCKS = 296;  // fixed grid of the two-stage reductions (deterministic)
+// fixed grids of the two-stage reductions (deterministic): the PCG reductions and updates stream
+// n_lambda-long vectors with dependent (gathered) loads, so they take 8 CTAs per SM of 152; the
+// refinement check, whose finishing thread re-adds the first partials serially, keeps fewer
+constexpr int RED_BLOCKS = 1216;
+constexpr int RED_BLOCKS_IR = 296;
 
 // status codes written by kernels (first error wins)
 enum DevStatus { DS_OK = 0, DS_ZERO_PIVOT = 1, DS_TIMEOUT = 2, DS_BREAKDOWN = 3, DS_NONFINITE = 4 };
