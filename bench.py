@@ -306,7 +306,8 @@ def arm_options(args, precision):
         opts = (("solve_kernel", args.solve_kernel), ("solve_wpc", args.wpc), ("solve_chunk", args.chunk),
                 ("solve_cps", args.cps),
                 ("factor_fp64", args.factor_fp64), ("graph", args.graph), ("factor_nb", args.factor_nb),
-                ("explicit", args.explicit), ("precond_bf16", args.precond_bf16))
+                ("explicit", args.explicit), ("precond_bf16", args.precond_bf16),
+                ("explicit_df", args.explicit_df))
     return [(k, v) for k, v in opts if v is not None]
 
 
@@ -770,6 +771,8 @@ def main():
                     help="preconditioner (both arms); default: the workload's (Dirichlet)")
     ap.add_argument("--fp64-explicit", type=int, default=1, help="explicit operators in the FP64 arm")
     ap.add_argument("--precond-bf16", type=int, default=None, help="mixed arm: S_s tiles in BF16")
+    ap.add_argument("--explicit-df", type=int, default=None,
+                    help="mixed arm: 1 build the FP64 F_s in two-float arithmetic, 0 in FP64")
     ap.add_argument("--graph", type=int, default=None, help="1: one CUDA graph launch per time step")
     ap.add_argument("--learned", type=int, default=1, help="mixed arm: learned lambda_0 (trained in warm-up)")
     ap.add_argument("--learned-epochs", type=int, default=8)

@@ -389,6 +389,11 @@ fp_status fp_mlp_loss_grad(fp_handle *h, const float *x, const float *y, int row
  *                       stored as FP32 hi/lo pairs of its upper 32 x 32 tiles (FP32 arithmetic
  *                       with error-free products and sums, ~1e-14 relative) instead of the FP64
  *                       F_s; 0: the FP64 F_s
+ *   "explicit_df"  [1]  mixed precision with "explicit" and "factor_fp64": the FP64 F_s (source
+ *                       of the accurate applies' tiles) is built in two-float arithmetic on the
+ *                       FP32 units from the FP64 factor split into FP32 hi/lo pairs (error-free
+ *                       products and sums, ~2^-46 relative per operation); 0: FP64 arithmetic.
+ *                       Takes effect at the next fp_factor
  *   "coarse_2f"    [1]  mixed precision: the coarse projection multiplies by (G^T G)^{-1} stored
  *                       as FP32 hi/lo pairs of its upper 32 x 32 tiles (half the bytes, FP32
  *                       arithmetic with error-free products and sums, ~1e-14 relative); 0: the
@@ -445,6 +450,8 @@ typedef struct {
   /* device time of each explicit operator's multi-right-hand-side build (index 0 F_s, 1 S_s;
    * the parts of explicit_ms), milliseconds; 0 where not built */
   double mrhs_ms[2];
+  /* arithmetic of each build: 0 FP64, 1 FP32, 2 two-float (FP32 pairs, FP64 result); -1 not built */
+  int mrhs_prec[2];
 } fp_tuning;
 fp_status fp_get_tuning(const fp_handle *h, fp_tuning *out);
 

@@ -31,12 +31,13 @@ cudaError_t launch_band_solve_blk(bool fp32, int mmax, int grid, int wpc, int ch
 cudaError_t launch_band_linv(bool fp32, const BandTask *tasks, int ntask, const void *fac, void *linv,
                              cudaStream_t stream);
 cudaError_t launch_round_to_float(const double *src, float *dst, long long n, cudaStream_t stream);
-size_t mrhs_smem_bytes(bool fp32, int R, int LDp, int mt);
-cudaError_t launch_band_mrhs(bool fp32, int bmax, int mt, int grid, cudaStream_t st, const int *task_s,
+size_t mrhs_smem_bytes(int prec, int R, int LDp, int mt);
+cudaError_t launch_split_df(double *v, long long n, cudaStream_t st);
+cudaError_t launch_band_mrhs(int prec, int bmax, int mt, int grid, cudaStream_t st, const int *task_s,
                              const int *task_j0, int ntask, DevTopo D, const void *fac, const void *linv,
                              const long long *linv_off, const double *csr, int kind, void *scratch, long long sstride,
                              int *counter, void *out, const long long *out_off, int R, int LDp);
-int mrhs_blocks_per_sm(bool fp32, int bmax, int mt, int R, int LDp);
+int mrhs_blocks_per_sm(int prec, int bmax, int mt, int R, int LDp);
 int mrhs_nr(int b, int mt);
 cudaError_t launch_mrhs_symmetrize(bool fp32, DevTopo D, int S, void *out, const long long *out_off, int mt,
                                    cudaStream_t st);
@@ -160,6 +161,7 @@ struct fp_handle {
   double *opF64 = nullptr;              // mixed precision: F_s in FP64 for the accurate applies
   float *opF2 = nullptr;                // ... and as two-float (hi/lo FP32) symmetric tiles
   int explicit_2f = 1;                  // option: accurate mixed-precision F applies from opF2
+  int explicit_df = 1;                  // option: opF64 built in two-float arithmetic (FP32 units)
   int precond_bf16 = 1;                 // option: mixed precision's S_s tiles in BF16
   int opS_bf16 = 0;                     // the stored S_s tiles are BF16
   const long long *op_off = nullptr, *tile_off = nullptr, *linv_off_dev = nullptr;
@@ -874,7 +876,7 @@ fp_status build_features(fp_handle *h) {
 }
 
 fp_status choose_nb(fp_handle *h, bool dbl, const BandTask *tasks, void *buf, int *nb_out);
-fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, int kind, void *out);
+fp_status run_mrhs(fp_handle *h, int prec, const void *fac, const void *linv, int kind, void *out);
 fp_status alloc_op(fp_handle *h, void **p, size_t bytes);
 
 // FP32 factorisation on the tensor cores (k_band_factor_tc): usable when the widest band's
@@ -949,7 +951,14 @@ fp_status factor_T(fp_handle *h) {
         // PCG loop's operator)
         st = alloc_op(h, (void **)&h->opF64, (size_t)h->op_total * 8);
         if (st == FP_OK) st = alloc_op(h, &h->opF, (size_t)h->tile_total * 4);
-        if (st == FP_OK) st = run_mrhs(h, false, tN, tL, 0, h->opF64);
+        if (st == FP_OK && h->explicit_df) {
+          // two-float arithmetic on the FP32 units: the FP64 factor (already rounded to FP32
+          // above) and its inverse blocks split in place
+          ee = launch_split_df(tN, (long long)nf, h->stream);
+          if (ee == cudaSuccess) ee = launch_split_df(tL, h->linv_total, h->stream);
+          if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
+        }
+        if (st == FP_OK) st = run_mrhs(h, h->explicit_df ? MRHS_DF : MRHS_FP64, tN, tL, 0, h->opF64);
         if (st == FP_OK) {
           ee = launch_pack_sym(true, h->D, h->T.S, h->opF64, h->op_off, (float *)h->opF, h->tile_off, h->stream);
           if (ee != cudaSuccess) { h->err = cudaGetErrorString(ee); st = FP_ERR_CUDA; }
@@ -1104,16 +1113,18 @@ fp_status autotune_solve(fp_handle *h) {
 // ---------------------------- explicit interface operators ------------------------------
 // One operator for every subdomain by the multi-right-hand-side band kernel: kind 0 F_s =
 // (K_s^+)_{bb} from Neumann factors, kind 1 S_s = K_bb - K_bi K_ii^{-1} K_ib from Dirichlet
-// factors, in the precision of the factors given (fp32).  out: op_total entries.
-fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, int kind, void *out) {
+// factors, in the arithmetic prec (MRHS_FP64, MRHS_FP32, or MRHS_DF: factors and inverse blocks
+// split into two-float values, FP64 operator).  out: op_total entries (FP32 for MRHS_FP32, else FP64).
+fp_status run_mrhs(fp_handle *h, int prec, const void *fac, const void *linv, int kind, void *out) {
+  const bool fp32 = prec == MRHS_FP32;
   const size_t esz = fp32 ? 4 : 8;
   int bmax = 0, nmax = 0;
   for (const Template &t : h->T.tpl) { bmax = std::max(bmax, t.b); nmax = std::max(nmax, t.n); }
   const int R = (bmax + 64 + 31) / 32 * 32, LDp = h->ldmax + 4;
   // tiles of 32 right-hand sides, or 16 where the 32-wide window does not fit
   int mt = 32, w = 0;
-  int bps = h->explicit_tile == 16 ? 0 : mrhs_blocks_per_sm(fp32, bmax, 32, R, LDp);
-  if (bps < 1 && h->explicit_tile != 32) { mt = 16; w = 1; bps = mrhs_blocks_per_sm(fp32, bmax, 16, R, LDp); }
+  int bps = h->explicit_tile == 16 ? 0 : mrhs_blocks_per_sm(prec, bmax, 32, R, LDp);
+  if (bps < 1 && h->explicit_tile != 32) { mt = 16; w = 1; bps = mrhs_blocks_per_sm(prec, bmax, 16, R, LDp); }
   if (bps < 1) {
     h->err = "explicit operators: the band is too wide for the shared-memory window";
     return FP_ERR_INVALID;
@@ -1129,7 +1140,7 @@ fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, i
   CK(cudaEventRecord(h->ev[4], h->stream));
   cudaError_t e = cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
-    e = launch_band_mrhs(fp32, bmax, mt, grid, h->stream, h->mrhs_s[w], h->mrhs_j0[w], h->mrhs_ntask[w], h->D, fac,
+    e = launch_band_mrhs(prec, bmax, mt, grid, h->stream, h->mrhs_s[w], h->mrhs_j0[w], h->mrhs_ntask[w], h->D, fac,
                          linv, h->linv_off_dev, h->csr_val, kind, scratch, sstride, h->counter, out, h->op_off, R,
                          LDp);
   if (e == cudaSuccess) e = launch_mrhs_symmetrize(fp32, h->D, h->T.S, out, h->op_off, mt, h->stream);
@@ -1142,6 +1153,7 @@ fp_status run_mrhs(fp_handle *h, bool fp32, const void *fac, const void *linv, i
   cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]);
   h->tuning.explicit_ms += ms;
   h->tuning.mrhs_ms[kind] += ms;
+  h->tuning.mrhs_prec[kind] = prec;
   return FP_OK;
 }
 
@@ -1160,10 +1172,10 @@ fp_status build_explicit(fp_handle *h) {
   const bool need_S = h->precond_req == FP_PRECOND_DIRICHLET || h->precond_req == FP_PRECOND_AUTO;
   if (h->P.precision == FP_PREC_FP64) {
     TRY(alloc_op(h, &h->opF, (size_t)h->op_total * 8));
-    TRY(run_mrhs(h, false, h->facN, h->linvN, 0, h->opF));
+    TRY(run_mrhs(h, MRHS_FP64, h->facN, h->linvN, 0, h->opF));
     if (need_S) {
       TRY(alloc_op(h, &h->opS, (size_t)h->op_total * 8));
-      TRY(run_mrhs(h, false, h->facD, h->linvD, 1, h->opS));
+      TRY(run_mrhs(h, MRHS_FP64, h->facD, h->linvD, 1, h->opS));
     }
     h->ops_ready = 1;
     return FP_OK;
@@ -1174,14 +1186,14 @@ fp_status build_explicit(fp_handle *h) {
   CK(cudaMalloc(&full, (size_t)h->op_total * 4));
   fp_status st = FP_OK;
   if (!h->opF64_ready) {
-    st = run_mrhs(h, true, h->facN, h->linvN, 0, full);
+    st = run_mrhs(h, MRHS_FP32, h->facN, h->linvN, 0, full);
     if (st == FP_OK && launch_pack_sym(false, h->D, h->T.S, full, h->op_off, (float *)h->opF, h->tile_off,
                                        h->stream) != cudaSuccess) {
       h->err = "explicit operators: packing the symmetric tiles of F_s failed";
       st = FP_ERR_CUDA;
     }
   }
-  if (st == FP_OK && need_S) st = run_mrhs(h, true, h->facD, h->linvD, 1, full);
+  if (st == FP_OK && need_S) st = run_mrhs(h, MRHS_FP32, h->facD, h->linvD, 1, full);
   h->opS_bf16 = h->precond_bf16;
   if (st == FP_OK && need_S &&
       launch_pack_sym(false, h->D, h->T.S, full, h->op_off, h->opS, h->tile_off, h->stream, h->opS_bf16 != 0) !=
@@ -1769,6 +1781,7 @@ fp_status fp_factor(fp_handle *h) {
   for (int k = 0; k < 2; ++k) {
     h->tuning.mrhs_nr[k] = h->tuning.mrhs_mt[k] = h->tuning.mrhs_esz[k] = 0;
     h->tuning.mrhs_ms[k] = 0.0;
+    h->tuning.mrhs_prec[k] = -1;
   }
   CK(cudaMemsetAsync(h->ir_prev, 0, 2 * sizeof(double), h->stream));
   TRY(h->P.precision == FP_PREC_MIXED ? factor_T<float>(h) : factor_T<double>(h));
@@ -2307,6 +2320,7 @@ fp_status fp_set_option(fp_handle *h, const char *key, double value) {
   else if (k == "autotune") { if (v < 0 || v > 1) return bad(); h->autotune = v; }
   else if (k == "mlp_tc") { if (v < 0 || v > 1) return bad(); h->mlp_tc = v; }
   else if (k == "factor_tc") { if (v < 0 || v > 1) return bad(); h->factor_tc = v; }
+  else if (k == "explicit_df") { if (v < 0 || v > 1) return bad(); h->explicit_df = v; }
   else if (k == "precond_bf16") { if (v < 0 || v > 1) return bad(); h->precond_bf16 = v; }
   else if (k == "explicit_2f") { if (v < 0 || v > 1) return bad(); h->explicit_2f = v; }
   else if (k == "coarse_2f") { if (v < 0 || v > 1) return bad(); h->coarse_2f = v; }

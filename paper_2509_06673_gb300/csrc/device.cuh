@@ -116,6 +116,9 @@ enum RedOp { OP_STORE = 0, OP_PQ = 1, OP_RZ_INIT = 2, OP_RZ = 3, OP_RNORM = 4, O
 constexpr int RED_BLOCKS = 1216;
 constexpr int RED_BLOCKS_IR = 296;
 
+// arithmetic of the explicit operators' multi-right-hand-side build
+enum MrhsPrec { MRHS_FP64 = 0, MRHS_FP32 = 1, MRHS_DF = 2 };
+
 // status codes written by kernels (first error wins)
 enum DevStatus { DS_OK = 0, DS_ZERO_PIVOT = 1, DS_TIMEOUT = 2, DS_BREAKDOWN = 3, DS_NONFINITE = 4 };
 

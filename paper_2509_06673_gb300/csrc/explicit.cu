@@ -25,17 +25,72 @@ __device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
   v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
 }
 
+// Scalar arithmetic of the build, per element type.  float and double: plain FMAs (the same
+// values as the contracted a += x * y).  dfl: a two-float value h + l (the FP64 factor split
+// once, two_sum / TwoProduct by fma as in device.cuh), ~2^-46 relative per operation, which gives
+// F_s to FP64-like accuracy from FP32 instructions: GB300 issues FP64 FMAs at about 1/60 of the FP32
+// rate, and a two-float multiply-add costs 15 FP32 instructions.
+struct __align__(8) dfl {
+  float h, l;
+};
+template <typename T> __device__ __forceinline__ T num(double v);
+template <> __device__ __forceinline__ float num<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ double num<double>(double v) { return v; }
+template <> __device__ __forceinline__ dfl num<dfl>(double v) {
+  dfl r;
+  df_split(v, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ double to_double(float v) { return v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(dfl v) { return (double)v.h + (double)v.l; }
+template <typename TO, typename T> __device__ __forceinline__ TO out_of(T v) { return v; }
+template <> __device__ __forceinline__ double out_of<double, dfl>(dfl v) { return to_double(v); }
+// a += x * y
+__device__ __forceinline__ void fma_acc(float &a, float x, float y) { a = fmaf(x, y, a); }
+__device__ __forceinline__ void fma_acc(double &a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void fma_acc(dfl &a, dfl x, dfl y) {
+  const float p = x.h * y.h;
+  const float pe = fmaf(x.l, y.h, fmaf(x.h, y.l, fmaf(x.h, y.h, -p)));
+  float s, e;
+  two_sum(a.h, p, s, e);
+  e += a.l + pe;
+  a.h = s + e;
+  a.l = e - (a.h - s);
+}
+// a -= x * y
+__device__ __forceinline__ void fms_acc(float &a, float x, float y) { a = fmaf(-x, y, a); }
+__device__ __forceinline__ void fms_acc(double &a, double x, double y) { a = fma(-x, y, a); }
+__device__ __forceinline__ void fms_acc(dfl &a, dfl x, dfl y) { fma_acc(a, dfl{-x.h, -x.l}, y); }
+// a -= b
+__device__ __forceinline__ void sub_from(float &a, float b) { a -= b; }
+__device__ __forceinline__ void sub_from(double &a, double b) { a -= b; }
+__device__ __forceinline__ void sub_from(dfl &a, dfl b) { df_add(a.h, a.l, -b.h, -b.l); }
+// x * y
+__device__ __forceinline__ float mul(float x, float y) { return x * y; }
+__device__ __forceinline__ double mul(double x, double y) { return x * y; }
+__device__ __forceinline__ dfl mul(dfl x, dfl y) {
+  dfl r;
+  float hh, ll;
+  df_mul(x.h, x.l, y.h, y.l, hh, ll);
+  r.h = hh + ll;
+  r.l = ll - (r.h - hh);
+  return r;
+}
+
 // kind 0: F_s (right-hand sides e_{b_j}; fixed dofs of floating subdomains give zero
 // columns), kind 1: S_s (right-hand sides -K_{i, b_j} on interior rows, Dirichlet factor).
 // Task t = (subdomain task_s[t], first column task_j0[t]); MT right-hand sides per task
 // (32, or 16 where a 32-wide window does not fit in shared memory).  Thread layout: CG = MT/4
 // column groups of 4, RG = 256/CG row groups; NR = ceil(b / RG) rows per thread in the
 // forward coupling; only the first 32 row groups work on the 32-row diagonal blocks.
-template <typename T, int NR, int MT>
+// T: the arithmetic and storage type of factor, inverse blocks, window and scratch (float, double,
+// or dfl); TO: the operator's element type (T, or double for dfl).
+template <typename T, typename TO, int NR, int MT>
 __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int *task_j0, int ntask, DevTopo D,
                                                    const T *fac, const T *linv, const long long *linv_off,
                                                    const double *csr_val, int kind, T *scratch,
-                                                   long long scratch_stride, int *counter, T *out,
+                                                   long long scratch_stride, int *counter, TO *out,
                                                    const long long *out_off, int R, int LDp) {
   constexpr int CG = MT / 4, RG = 256 / CG;
   extern __shared__ unsigned char smraw[];
@@ -64,16 +119,16 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     const T *Li = linv + linv_off[s];
     auto fixed = [&](int d) { return t.floating && (d == t.fixed0 || d == t.fixed1 || d == t.fixed2); };
     // ---- right-hand sides into the scratch block (row r at Xs + r * MT) ----
-    for (long long i = tid; i < (long long)n * MT; i += blockDim.x) Xs[i] = T(0);
+    for (long long i = tid; i < (long long)n * MT; i += blockDim.x) Xs[i] = num<T>(0.0);
     __syncthreads();
     for (int jj = tid; jj < ncol; jj += blockDim.x) {
       const int c = bnd[j0 + jj];
       if (kind == 0) {
-        if (!fixed(c)) Xs[(long long)c * MT + jj] = T(1);
+        if (!fixed(c)) Xs[(long long)c * MT + jj] = num<T>(1.0);
       } else {
         for (int e = cptr[c]; e < cptr[c + 1]; ++e) {
           const int i = ccol[e];
-          if (!isb[i]) Xs[(long long)i * MT + jj] = T(-val[e]);
+          if (!isb[i]) Xs[(long long)i * MT + jj] = num<T>(-val[e]);
         }
       }
     }
@@ -102,14 +157,14 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       for (int idx = tid; idx < 1024; idx += blockDim.x) Lv[idx] = Li[(long long)k * 1024 + idx];
       __syncthreads();
       // diagonal block: y_k = Linv_k w_k (rows past n are never loaded: c < ncb)
-      T y[4] = {T(0), T(0), T(0), T(0)};
+      T y[4] = {num<T>(0.0), num<T>(0.0), num<T>(0.0), num<T>(0.0)};
       if (rg < 32) {
         for (int c = 0; c < ncb; ++c) {
           const T l = Lv[rg * 32 + c];
           T w[4];
           ld4(Wn + ((r0 + c) % R) * MT + 4 * cg, w);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) y[q] += l * w[q];
+          for (int q = 0; q < 4; ++q) fma_acc(y[q], l, w[q]);
         }
       }
       __syncthreads();
@@ -120,7 +175,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           wr[q] = y[q];
-          xr[q] = y[q] * dinv;
+          xr[q] = mul(y[q], dinv);
         }
       }
       __syncthreads();
@@ -129,7 +184,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
 #pragma unroll
       for (int i = 0; i < NR; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = T(0);
+        for (int q = 0; q < 4; ++q) acc[i][q] = num<T>(0.0);
       for (int c = 0; c < ncb; ++c) {
         T yc[4];
         ld4(Wn + ((r0 + c) % R) * MT + 4 * cg, yc);
@@ -137,9 +192,9 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
           const int r = r0 + 32 + rg + RG * i;
-          const T l = (r < rend && r - (r0 + c) <= b) ? col[r % LD] : T(0);
+          const T l = (r < rend && r - (r0 + c) <= b) ? col[r % LD] : num<T>(0.0);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[i][q] += l * yc[q];
+          for (int q = 0; q < 4; ++q) fma_acc(acc[i][q], l, yc[q]);
         }
       }
 #pragma unroll
@@ -148,7 +203,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
         if (r < rend) {
           T *wr = Wn + (r % R) * MT + 4 * cg;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) wr[q] -= acc[i][q];
+          for (int q = 0; q < 4; ++q) sub_from(wr[q], acc[i][q]);
         }
       }
       __syncthreads();
@@ -162,17 +217,17 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       }
       for (int idx = tid; idx < 1024; idx += blockDim.x) Lv[idx] = Li[(long long)k * 1024 + idx];
       __syncthreads();
-      T tv[4] = {T(0), T(0), T(0), T(0)};
+      T tv[4] = {num<T>(0.0), num<T>(0.0), num<T>(0.0), num<T>(0.0)};
       if (rg < ncb) {
         ld4(Xs + (long long)(r0 + rg) * MT + 4 * cg, tv);
         const T *col = Fc + rg * LDp;
         const int j = r0 + rg;
         for (int r = r0 + 32; r < rtop; ++r) {
-          const T l = (r - j <= b) ? col[r % LD] : T(0);
+          const T l = (r - j <= b) ? col[r % LD] : num<T>(0.0);
           T x4[4];
           ld4(Wn + (r % R) * MT + 4 * cg, x4);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) tv[q] -= l * x4[q];
+          for (int q = 0; q < 4; ++q) fms_acc(tv[q], l, x4[q]);
         }
       }
       if (rg < 32) {
@@ -181,7 +236,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       }
       __syncthreads();
       // within the block: x_k = Linv_k^T t
-      T x[4] = {T(0), T(0), T(0), T(0)};
+      T x[4] = {num<T>(0.0), num<T>(0.0), num<T>(0.0), num<T>(0.0)};
       if (rg < 32) {
 #pragma unroll 8
         for (int c = 0; c < 32; ++c) {
@@ -189,7 +244,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
           T tc[4];
           ld4(Tt + c * MT + 4 * cg, tc);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) x[q] += l * tc[q];
+          for (int q = 0; q < 4; ++q) fma_acc(x[q], l, tc[q]);
         }
       }
       if (rg < ncb) {
@@ -204,13 +259,13 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       __syncthreads();
     }
     // ---- the operator's columns j0 .. j0 + ncol - 1 ----
-    T *O = out + out_off[s];
+    TO *O = out + out_off[s];
     const int mp = (m + 3) & ~3;  // row stride (padded to 4 for vector loads)
     const int mlow = m - j0;  // rows a = j0 .. m - 1
     if (kind == 0) {
       for (int idx = tid; idx < mlow * ncol; idx += blockDim.x) {
         const int a = j0 + idx / ncol, jj = idx % ncol;
-        O[(long long)a * mp + j0 + jj] = Xs[(long long)bnd[a] * MT + jj];
+        O[(long long)a * mp + j0 + jj] = out_of<TO>(Xs[(long long)bnd[a] * MT + jj]);
       }
     } else {
       // S[a][j] = sum_c K[b_a][c] (y_j[c] + [c == b_j]);  y_j vanishes on the rows of b
@@ -220,9 +275,9 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
         double acc = 0.0;
         for (int e = cptr[row]; e < cptr[row + 1]; ++e) {
           const int c = ccol[e];
-          acc += val[e] * ((double)Xs[(long long)c * MT + jj] + (c == cj ? 1.0 : 0.0));
+          acc += val[e] * (to_double(Xs[(long long)c * MT + jj]) + (c == cj ? 1.0 : 0.0));
         }
-        O[(long long)a * mp + j0 + jj] = T(acc);
+        O[(long long)a * mp + j0 + jj] = TO(acc);
       }
     }
     __syncthreads();
@@ -602,16 +657,16 @@ cudaError_t launch_explicit_apply_sym(DevTopo D, int S, int mmax_bnd, const void
 }
 
 // ------------------------------------ launchers --------------------------------------
-template <typename T, int NR, int MT>
+template <typename T, typename TO, int NR, int MT>
 static cudaError_t launch_mrhs_T(int grid, cudaStream_t st, const int *ts, const int *tj, int ntask, DevTopo D,
                                  const T *fac, const T *linv, const long long *loff, const double *csr, int kind,
-                                 T *scratch, long long sstride, int *counter, T *out, const long long *ooff, int R,
+                                 T *scratch, long long sstride, int *counter, TO *out, const long long *ooff, int R,
                                  int LDp, size_t smem) {
   cudaError_t e =
-      cudaFuncSetAttribute(k_band_mrhs<T, NR, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_band_mrhs<T, TO, NR, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_band_mrhs<T, NR, MT><<<grid, 256, smem, st>>>(ts, tj, ntask, D, fac, linv, loff, csr, kind, scratch, sstride,
-                                                  counter, out, ooff, R, LDp);
+  k_band_mrhs<T, TO, NR, MT><<<grid, 256, smem, st>>>(ts, tj, ntask, D, fac, linv, loff, csr, kind, scratch,
+                                                      sstride, counter, out, ooff, R, LDp);
   return cudaGetLastError();
 }
 
@@ -622,8 +677,9 @@ cudaError_t launch_mrhs_symmetrize(bool fp32, DevTopo D, int S, void *out, const
   return cudaGetLastError();
 }
 
-size_t mrhs_smem_bytes(bool fp32, int R, int LDp, int mt) {
-  const size_t esz = fp32 ? 4 : 8;
+// prec: MRHS_FP64, MRHS_FP32 or MRHS_DF (two-float arithmetic, FP64 operator)
+size_t mrhs_smem_bytes(int prec, int R, int LDp, int mt) {
+  const size_t esz = prec == MRHS_FP32 ? 4 : 8;
   return esz * ((size_t)R * mt + 32 * (size_t)LDp + 1024 + 32 * (size_t)mt);
 }
 
@@ -634,48 +690,69 @@ int mrhs_nr(int b, int mt) {
   return nr <= 4 ? 4 : nr <= 8 ? 8 : nr <= 12 ? 12 : nr <= 16 ? 16 : 0;
 }
 
-template <typename T, int MT>
+template <typename T, typename TO, int MT>
 static const void *mrhs_fn(int nr) {
-  return nr == 4 ? (const void *)k_band_mrhs<T, 4, MT> : nr == 8 ? (const void *)k_band_mrhs<T, 8, MT>
-         : nr == 12 ? (const void *)k_band_mrhs<T, 12, MT> : (const void *)k_band_mrhs<T, 16, MT>;
+  return nr == 4 ? (const void *)k_band_mrhs<T, TO, 4, MT> : nr == 8 ? (const void *)k_band_mrhs<T, TO, 8, MT>
+         : nr == 12 ? (const void *)k_band_mrhs<T, TO, 12, MT> : (const void *)k_band_mrhs<T, TO, 16, MT>;
 }
 
-cudaError_t launch_band_mrhs(bool fp32, int bmax, int mt, int grid, cudaStream_t st, const int *task_s,
+cudaError_t launch_band_mrhs(int prec, int bmax, int mt, int grid, cudaStream_t st, const int *task_s,
                              const int *task_j0, int ntask, DevTopo D, const void *fac, const void *linv,
                              const long long *linv_off, const double *csr, int kind, void *scratch, long long sstride,
                              int *counter, void *out, const long long *out_off, int R, int LDp) {
-  const size_t smem = mrhs_smem_bytes(fp32, R, LDp, mt);
+  const size_t smem = mrhs_smem_bytes(prec, R, LDp, mt);
   const int nr = mrhs_nr(bmax, mt);
   if (nr == 0 || (mt != 32 && mt != 16)) return cudaErrorInvalidValue;
-#define FP_MRHS(TT, N, M)                                                                                       \
-  return launch_mrhs_T<TT, N, M>(grid, st, task_s, task_j0, ntask, D, (const TT *)fac, (const TT *)linv, linv_off, \
-                                 csr, kind, (TT *)scratch, sstride, counter, (TT *)out, out_off, R, LDp, smem)
-#define FP_MRHS_NR(TT, M)              \
-  if (nr == 4) FP_MRHS(TT, 4, M);      \
-  if (nr == 8) FP_MRHS(TT, 8, M);      \
-  if (nr == 12) FP_MRHS(TT, 12, M);    \
-  FP_MRHS(TT, 16, M)
-  if (fp32) {
-    if (mt == 32) { FP_MRHS_NR(float, 32); }
-    FP_MRHS_NR(float, 16);
+#define FP_MRHS(TT, TTO, N, M)                                                                                    \
+  return launch_mrhs_T<TT, TTO, N, M>(grid, st, task_s, task_j0, ntask, D, (const TT *)fac, (const TT *)linv,     \
+                                      linv_off, csr, kind, (TT *)scratch, sstride, counter, (TTO *)out, out_off, R, \
+                                      LDp, smem)
+#define FP_MRHS_NR(TT, TTO, M)            \
+  if (nr == 4) FP_MRHS(TT, TTO, 4, M);    \
+  if (nr == 8) FP_MRHS(TT, TTO, 8, M);    \
+  if (nr == 12) FP_MRHS(TT, TTO, 12, M);  \
+  FP_MRHS(TT, TTO, 16, M)
+  if (prec == MRHS_FP32) {
+    if (mt == 32) { FP_MRHS_NR(float, float, 32); }
+    FP_MRHS_NR(float, float, 16);
   }
-  if (mt == 32) { FP_MRHS_NR(double, 32); }
-  FP_MRHS_NR(double, 16);
+  if (prec == MRHS_DF) {
+    if (mt == 32) { FP_MRHS_NR(dfl, double, 32); }
+    FP_MRHS_NR(dfl, double, 16);
+  }
+  if (mt == 32) { FP_MRHS_NR(double, double, 32); }
+  FP_MRHS_NR(double, double, 16);
 #undef FP_MRHS_NR
 #undef FP_MRHS
 }
 
 // resident CTAs per SM of the build kernel at this shared-memory size (0: does not fit)
-int mrhs_blocks_per_sm(bool fp32, int bmax, int mt, int R, int LDp) {
-  const size_t smem = mrhs_smem_bytes(fp32, R, LDp, mt);
+int mrhs_blocks_per_sm(int prec, int bmax, int mt, int R, int LDp) {
+  const size_t smem = mrhs_smem_bytes(prec, R, LDp, mt);
   const int nr = mrhs_nr(bmax, mt);
   if (nr == 0 || smem > 227 * 1024) return 0;
-  const void *f = fp32 ? (mt == 32 ? mrhs_fn<float, 32>(nr) : mrhs_fn<float, 16>(nr))
-                       : (mt == 32 ? mrhs_fn<double, 32>(nr) : mrhs_fn<double, 16>(nr));
+  const void *f = prec == MRHS_FP32 ? (mt == 32 ? mrhs_fn<float, float, 32>(nr) : mrhs_fn<float, float, 16>(nr))
+                  : prec == MRHS_DF ? (mt == 32 ? mrhs_fn<dfl, double, 32>(nr) : mrhs_fn<dfl, double, 16>(nr))
+                                    : (mt == 32 ? mrhs_fn<double, double, 32>(nr) : mrhs_fn<double, double, 16>(nr));
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, 256, smem) != cudaSuccess) return 0;
   return nb;
+}
+
+// Splits n FP64 values in place into two-float values (h, l) occupying the same 8 bytes.
+__global__ void k_split_df(double *v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    dfl r;
+    df_split(v[i], r.h, r.l);
+    reinterpret_cast<dfl *>(v)[i] = r;
+  }
+}
+
+cudaError_t launch_split_df(double *v, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_split_df<<<1216, 256, 0, st>>>(v, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_explicit_apply(bool fp32, DevTopo D, int S, int mmax_bnd, const void *ops, const long long *op_off,

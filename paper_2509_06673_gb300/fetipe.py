@@ -76,7 +76,7 @@ class Tuning(ctypes.Structure):
                 ("precond_rate", ctypes.c_double * 2), ("precond_ms_per_it", ctypes.c_double * 2),
                 ("solve_mmax", ctypes.c_int), ("mrhs_nr", ctypes.c_int * 2), ("mrhs_mt", ctypes.c_int * 2),
                 ("mrhs_esz", ctypes.c_int * 2), ("factor_tc_ms", ctypes.c_double * 2),
-                ("mrhs_ms", ctypes.c_double * 2)]
+                ("mrhs_ms", ctypes.c_double * 2), ("mrhs_prec", ctypes.c_int * 2)]
 
 
 class StepStats(ctypes.Structure):
@@ -396,7 +396,7 @@ class Solver:
         t = Tuning()
         self._check(_lib.fp_get_tuning(self._h, ctypes.byref(t)))
         out = {k: getattr(t, k) for k, _ in Tuning._fields_}
-        for k in ("precond_rate", "precond_ms_per_it", "mrhs_nr", "mrhs_mt", "mrhs_esz", "factor_tc_ms", "mrhs_ms"):
+        for k in ("precond_rate", "precond_ms_per_it", "mrhs_nr", "mrhs_mt", "mrhs_esz", "factor_tc_ms", "mrhs_ms", "mrhs_prec"):
             out[k] = list(out[k])
         return out
 

@@ -220,3 +220,36 @@ def test_bf16_preconditioner_steps(F):
                     assert np.abs(gp - p).max() < TOL * max(np.abs(p).max(), 1e-300), (bf, n, s)
         sol.close()
     assert sum(its[1]) <= 1.25 * sum(its[0]) + 4, its
+
+
+def test_two_float_build_of_F(F):
+    """The FP64 F_s behind the accurate applies built in two-float arithmetic from the FP64
+    factor split into hi/lo FP32 pairs (explicit_df = 1, the default) against the same build in
+    FP64 arithmetic (explicit_df = 0) and the oracle's F, at lambda = 499 (log-normal
+    permeability): the accurate F applies agree to 1e-12, and the mixed steps still match the
+    oracle's monolithic solution at 1e-8."""
+    from oracle.monolithic import Discretization, solve_monolithic
+    from oracle.feti import FETI
+    case = CASES[1]
+    disc = Discretization(case)
+    fe = FETI(case, disc)
+    out = {}
+    for df in (1, 0):
+        sol = F.Solver(case)
+        sol.set_option("explicit", 1)
+        sol.set_option("explicit_df", df)
+        sol.set_option("ir_eps", 1e-15)
+        sol.assemble()
+        sol.factor()
+        assert sol.tuning()["mrhs_prec"][0] == (2 if df else 0)
+        v = np.random.default_rng(7).normal(size=sol.sizes.n_lambda)
+        out[df] = sol.apply_F(v)
+        assert _rel(out[df], fe.F(v)) < 1e-12, df
+        if df:
+            mono = solve_monolithic(case, disc)
+            for n in range(case.n_steps):
+                st = sol.step()
+                assert st["true_rel_residual"] <= case.tol
+                assert _rel(sol.get_lambda(), mono[n]["lambda"]) < TOL, n
+        sol.close()
+    assert _rel(out[1], out[0]) < 1e-12
