@@ -46,22 +46,30 @@ __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(dfl v) { return (double)v.h + (double)v.l; }
 template <typename TO, typename T> __device__ __forceinline__ TO out_of(T v) { return v; }
 template <> __device__ __forceinline__ double out_of<double, dfl>(dfl v) { return to_double(v); }
-// a += x * y
-__device__ __forceinline__ void fma_acc(float &a, float x, float y) { a = fmaf(x, y, a); }
-__device__ __forceinline__ void fma_acc(double &a, double x, double y) { a = fma(x, y, a); }
-__device__ __forceinline__ void fma_acc(dfl &a, dfl x, dfl y) {
+// Long sums: a += x * y with the two-float sum left unnormalised (the high part takes the exact
+// TwoSum, the low part collects its error and the product's), so the loop-carried chain is one
+// addition per part; norm() restores h + l with |l| <= ulp(h) / 2 before the value is used.
+// float and double: the plain FMA.
+__device__ __forceinline__ void fma_lazy(float &a, float x, float y) { a = fmaf(x, y, a); }
+__device__ __forceinline__ void fma_lazy(double &a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void fma_lazy(dfl &a, dfl x, dfl y) {
   const float p = x.h * y.h;
   const float pe = fmaf(x.l, y.h, fmaf(x.h, y.l, fmaf(x.h, y.h, -p)));
   float s, e;
   two_sum(a.h, p, s, e);
-  e += a.l + pe;
-  a.h = s + e;
-  a.l = e - (a.h - s);
+  a.h = s;
+  a.l += e + pe;
 }
-// a -= x * y
-__device__ __forceinline__ void fms_acc(float &a, float x, float y) { a = fmaf(-x, y, a); }
-__device__ __forceinline__ void fms_acc(double &a, double x, double y) { a = fma(-x, y, a); }
-__device__ __forceinline__ void fms_acc(dfl &a, dfl x, dfl y) { fma_acc(a, dfl{-x.h, -x.l}, y); }
+__device__ __forceinline__ void fms_lazy(float &a, float x, float y) { a = fmaf(-x, y, a); }
+__device__ __forceinline__ void fms_lazy(double &a, double x, double y) { a = fma(-x, y, a); }
+__device__ __forceinline__ void fms_lazy(dfl &a, dfl x, dfl y) { fma_lazy(a, dfl{-x.h, -x.l}, y); }
+__device__ __forceinline__ void norm(float &) {}
+__device__ __forceinline__ void norm(double &) {}
+__device__ __forceinline__ void norm(dfl &a) {
+  const float h = a.h + a.l;
+  a.l = a.l - (h - a.h);
+  a.h = h;
+}
 // a -= b
 __device__ __forceinline__ void sub_from(float &a, float b) { a -= b; }
 __device__ __forceinline__ void sub_from(double &a, double b) { a -= b; }
@@ -76,6 +84,19 @@ __device__ __forceinline__ dfl mul(dfl x, dfl y) {
   r.h = hh + ll;
   r.l = ll - (r.h - hh);
   return r;
+}
+
+// Copies ncb rows of LD elements (stride LD in global, LDp in shared memory; LD a multiple of 32,
+// LDp of 4, so every row starts 16-byte aligned on both sides) with 16-byte loads, one warp per row.
+template <typename T>
+__device__ __forceinline__ void stage_rows(T *dst, int LDp, const T *src, int LD, int ncb) {
+  constexpr int V = 16 / sizeof(T);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < ncb; c += nw) {
+    const uint4 *sp = reinterpret_cast<const uint4 *>(src + (long long)c * LD);
+    uint4 *dp = reinterpret_cast<uint4 *>(dst + (size_t)c * LDp);
+    for (int v = lane; v < LD / V; v += 32) dp[v] = sp[v];
+  }
 }
 
 // kind 0: F_s (right-hand sides e_{b_j}; fixed dofs of floating subdomains give zero
@@ -93,7 +114,7 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
                                                    long long scratch_stride, int *counter, TO *out,
                                                    const long long *out_off, int R, int LDp) {
   constexpr int CG = MT / 4, RG = 256 / CG;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   T *Wn = reinterpret_cast<T *>(smraw);  // R x MT window
   T *Fc = Wn + (size_t)R * MT;           // 32 x LDp staged factor columns
   T *Lv = Fc + (size_t)32 * LDp;         // 32 x 32 inverse diagonal block
@@ -150,22 +171,23 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
         Wn[(r % R) * MT + q] = Xs[(long long)r * MT + q];
       }
       hi = max(hi, rend);
-      for (int idx = tid; idx < ncb * LD; idx += blockDim.x) {
-        const int c = idx / LD, sl = idx - c * LD;
-        Fc[c * LDp + sl] = F[(long long)(r0 + c) * LD + sl];
-      }
-      for (int idx = tid; idx < 1024; idx += blockDim.x) Lv[idx] = Li[(long long)k * 1024 + idx];
+      stage_rows(Fc, LDp, F + (long long)r0 * LD, LD, ncb);
+      stage_rows(Lv, 32, Li + (long long)k * 1024, 32, 32);
       __syncthreads();
+      const int rw0 = r0 % R;  // window slot of row r0 (rows r0 .. r0 + 31 never wrap past R twice)
       // diagonal block: y_k = Linv_k w_k (rows past n are never loaded: c < ncb)
       T y[4] = {num<T>(0.0), num<T>(0.0), num<T>(0.0), num<T>(0.0)};
       if (rg < 32) {
         for (int c = 0; c < ncb; ++c) {
           const T l = Lv[rg * 32 + c];
           T w[4];
-          ld4(Wn + ((r0 + c) % R) * MT + 4 * cg, w);
+          const int rw = rw0 + c < R ? rw0 + c : rw0 + c - R;
+          ld4(Wn + rw * MT + 4 * cg, w);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) fma_acc(y[q], l, w[q]);
+          for (int q = 0; q < 4; ++q) fma_lazy(y[q], l, w[q]);
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) norm(y[q]);
       }
       __syncthreads();
       if (rg < ncb) {
@@ -185,22 +207,28 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
       for (int i = 0; i < NR; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][q] = num<T>(0.0);
+      int sl[NR];  // slot of row r0 + 32 + rg + RG i in a factor column
+#pragma unroll
+      for (int i = 0; i < NR; ++i) sl[i] = (r0 + 32 + rg + RG * i) % LD;
       for (int c = 0; c < ncb; ++c) {
         T yc[4];
-        ld4(Wn + ((r0 + c) % R) * MT + 4 * cg, yc);
+        const int rw = rw0 + c < R ? rw0 + c : rw0 + c - R;
+        ld4(Wn + rw * MT + 4 * cg, yc);
         const T *col = Fc + c * LDp;
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
           const int r = r0 + 32 + rg + RG * i;
-          const T l = (r < rend && r - (r0 + c) <= b) ? col[r % LD] : num<T>(0.0);
+          const T l = (r < rend && r - (r0 + c) <= b) ? col[sl[i]] : num<T>(0.0);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) fma_acc(acc[i][q], l, yc[q]);
+          for (int q = 0; q < 4; ++q) fma_lazy(acc[i][q], l, yc[q]);
         }
       }
 #pragma unroll
       for (int i = 0; i < NR; ++i) {
         const int r = r0 + 32 + rg + RG * i;
         if (r < rend) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) norm(acc[i][q]);
           T *wr = Wn + (r % R) * MT + 4 * cg;
 #pragma unroll
           for (int q = 0; q < 4; ++q) sub_from(wr[q], acc[i][q]);
@@ -211,24 +239,27 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
     // ---- backward sweep: L^T x = z; x rows kept in the window and written to Xs ----
     for (int k = nb - 1; k >= k0; --k) {
       const int r0 = 32 * k, ncb = min(32, n - r0), rtop = min(n, r0 + 32 + b);
-      for (int idx = tid; idx < ncb * LD; idx += blockDim.x) {
-        const int c = idx / LD, sl = idx - c * LD;
-        Fc[c * LDp + sl] = F[(long long)(r0 + c) * LD + sl];
-      }
-      for (int idx = tid; idx < 1024; idx += blockDim.x) Lv[idx] = Li[(long long)k * 1024 + idx];
+      stage_rows(Fc, LDp, F + (long long)r0 * LD, LD, ncb);
+      stage_rows(Lv, 32, Li + (long long)k * 1024, 32, 32);
       __syncthreads();
       T tv[4] = {num<T>(0.0), num<T>(0.0), num<T>(0.0), num<T>(0.0)};
       if (rg < ncb) {
         ld4(Xs + (long long)(r0 + rg) * MT + 4 * cg, tv);
         const T *col = Fc + rg * LDp;
         const int j = r0 + rg;
+        // slots of row r in a factor column (mod LD) and in the window (mod R), stepped with r
+        int rl = (r0 + 32) % LD, rw = (r0 + 32) % R;
         for (int r = r0 + 32; r < rtop; ++r) {
-          const T l = (r - j <= b) ? col[r % LD] : num<T>(0.0);
+          const T l = (r - j <= b) ? col[rl] : num<T>(0.0);
           T x4[4];
-          ld4(Wn + (r % R) * MT + 4 * cg, x4);
+          ld4(Wn + rw * MT + 4 * cg, x4);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) fms_acc(tv[q], l, x4[q]);
+          for (int q = 0; q < 4; ++q) fms_lazy(tv[q], l, x4[q]);
+          if (++rl == LD) rl = 0;
+          if (++rw == R) rw = 0;
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) norm(tv[q]);
       }
       if (rg < 32) {
 #pragma unroll
@@ -244,8 +275,10 @@ __global__ void __launch_bounds__(256) k_band_mrhs(const int *task_s, const int 
           T tc[4];
           ld4(Tt + c * MT + 4 * cg, tc);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) fma_acc(x[q], l, tc[q]);
+          for (int q = 0; q < 4; ++q) fma_lazy(x[q], l, tc[q]);
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) norm(x[q]);
       }
       if (rg < ncb) {
         T *wr = Wn + ((r0 + rg) % R) * MT + 4 * cg;
