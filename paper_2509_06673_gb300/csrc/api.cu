@@ -59,6 +59,8 @@ __global__ void k_dot(const double *, const double *, long long, double *, unsig
                       double *, int);
 __global__ void k_pcg_update(double *, double *, const double *, const double *, long long, double *, unsigned *,
                              double *, int *);
+__global__ void k_pcg_update_w(DevTopo, double *, double *, const double *, const double *, double *, double *,
+                               unsigned *, double *, int *);
 __global__ void k_pcg_pupdate(double *, const double *, long long, const double *, const int *);
 __global__ void k_lincomb(double *, const double *, double, const double *, double, long long, const int *);
 __global__ void k_scatter(DevTopo, const double *, double, double *, int, const int *, int);
@@ -733,18 +735,19 @@ fp_status apply_F(fp_handle *h, const double *v, double *out, const int *fl, boo
   return FP_OK;
 }
 
-fp_status apply_M_lumped(fp_handle *h, const double *v, double *out, const int *fl);
+fp_status apply_M_lumped(fp_handle *h, const double *v, double *out, const int *fl, bool w_done);
 
-// out = W B S B^T W v  (Eq. (3.5) with the scaling W)
-fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
+// out = W B S B^T W v  (Eq. (3.5) with the scaling W).  w_done: t1 already holds W v (the PCG
+// update kernel formed it), so the first scaling is skipped.
+fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl, bool w_done = false) {
   const int nl = h->T.n_lambda;
   const int ng = (int)h->T.wgrp_first.size();
   if (h->P.precond == FP_PRECOND_NONE) {
     if (out != v) CK(cudaMemcpyAsync(out, v, nl * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     return FP_OK;
   }
-  if (h->P.precond == FP_PRECOND_LUMPED) return apply_M_lumped(h, v, out, fl);
-  k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
+  if (h->P.precond == FP_PRECOND_LUMPED) return apply_M_lumped(h, v, out, fl, w_done);
+  if (!w_done) k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
   const bool fused = h->ops_ready && h->P.precision == FP_PREC_MIXED;  // tiled apply forms B^T W v itself
   if (!fused) k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl, h->ops_ready ? 0 : 1);
   CKL();
@@ -772,10 +775,10 @@ fp_status apply_M(fp_handle *h, const double *v, double *out, const int *fl) {
 
 // out = W B K_bb B^T W v: the lumped preconditioner (Sec. 3.3), the local matrices' interface
 // block in place of the Schur complement (no local solve)
-fp_status apply_M_lumped(fp_handle *h, const double *v, double *out, const int *fl) {
+fp_status apply_M_lumped(fp_handle *h, const double *v, double *out, const int *fl, bool w_done) {
   const int nl = h->T.n_lambda;
   const int ng = (int)h->T.wgrp_first.size();
-  k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
+  if (!w_done) k_wscale<<<(ng + 255) / 256, 256, 0, h->stream>>>(h->D, v, h->t1, fl);
   k_scatter<<<h->T.S, 256, 0, h->stream>>>(h->D, h->t1, 1.0, h->XP, 0, fl, 1);
   k_bnd_apply<<<h->T.S, 256, h->nbnd_max * sizeof(double), h->stream>>>(h->D, h->csr_val, nullptr, h->XP, fl);
   k_gather<<<(nl + 255) / 256, 256, 0, h->stream>>>(h->D, h->XP, h->t2, fl);
@@ -1392,9 +1395,17 @@ fp_status pcg_iteration(fp_handle *h) {
   cudaStream_t s = h->stream;
   TRY(apply_F(h, h->p, h->q, h->fl, false));
   TRY(apply_P_dot(h, h->q, h->q, h->p, OP_PQ));
-  k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
-  CKL();
-  TRY(apply_M(h, h->r, h->z, h->fl));
+  if (h->P.precond == FP_PRECOND_NONE) {
+    k_pcg_update<<<RED_BLOCKS, 256, 0, s>>>(h->lam, h->r, h->p, h->q, nl, h->partial, h->red_counter, h->sc, h->fl);
+    CKL();
+    TRY(apply_M(h, h->r, h->z, h->fl));
+  } else {
+    // the update also forms t1 = W r, the preconditioner's first step
+    k_pcg_update_w<<<RED_BLOCKS, 256, 0, s>>>(h->D, h->lam, h->r, h->p, h->q, h->t1, h->partial, h->red_counter,
+                                             h->sc, h->fl);
+    CKL();
+    TRY(apply_M(h, h->r, h->z, h->fl, true));
+  }
   TRY(apply_P_dot(h, h->z, h->z, h->r, OP_RZ));
   k_pcg_pupdate<<<(nl + 255) / 256, 256, 0, s>>>(h->p, h->z, nl, h->sc, h->fl);
   CKL();

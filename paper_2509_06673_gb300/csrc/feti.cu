@@ -114,6 +114,24 @@ __global__ void k_dot(const double *a, const double *b, long long n, double *par
   }
 }
 
+// out[0 .. m) = W_g v for one group of W = (B B^T)^{-1}: per node component a chain of m <= 3
+// rows whose B B^T is tridiag(-1, 2, -1), its inverse in closed form (multiplications by the
+// constant reciprocals: GB300's FP64 divide is a long instruction sequence; 1/4 is exact, 1/3
+// rounds once)
+__device__ __forceinline__ void wscale_group(const double *v, int m, double *out) {
+  constexpr double third = 1.0 / 3.0;
+  if (m == 1) {
+    out[0] = 0.5 * v[0];
+  } else if (m == 2) {
+    out[0] = (2 * v[0] + v[1]) * third;
+    out[1] = (v[0] + 2 * v[1]) * third;
+  } else {
+    out[0] = (3 * v[0] + 2 * v[1] + v[2]) * 0.25;
+    out[1] = (2 * v[0] + 4 * v[1] + 2 * v[2]) * 0.25;
+    out[2] = (v[0] + 2 * v[1] + 3 * v[2]) * 0.25;
+  }
+}
+
 // lambda += alpha p; r -= alpha q; then ||r||^2 -> stop test (Algorithm 1, lines 5-6)
 __global__ void k_pcg_update(double *lam, double *r, const double *p, const double *q, long long n,
                              double *partial, unsigned *counter, double *sc, int *fl) {
@@ -125,6 +143,34 @@ __global__ void k_pcg_update(double *lam, double *r, const double *p, const doub
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
     s += ri * ri;
+  }
+  double tot;
+  if (finish_reduction(s, partial, counter, tot)) apply_op(OP_RNORM, tot, sc, fl);
+}
+
+// k_pcg_update followed by the first step of the preconditioner (Eq. (3.5)): t = W r, one
+// thread per group of W (the rows of one node component; the groups partition the
+// multipliers), the scaling of k_wscale on the updated residual.  One launch instead of two.
+__global__ void k_pcg_update_w(DevTopo D, double *lam, double *r, const double *p, const double *q, double *t,
+                               double *partial, unsigned *counter, double *sc, int *fl) {
+  if (fl[FL_DONE]) return;
+  const double alpha = sc[SC_ALPHA];
+  double s = 0.0;
+  for (int gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < D.nwgrp; gidx += gridDim.x * blockDim.x) {
+    const int f = D.wgrp_first[gidx], m = D.wgrp_size[gidx];
+    double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // static indices keep v in registers
+      if (k < m) {
+        const int i = f + k;
+        lam[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        s += ri * ri;
+        v[k] = ri;
+      }
+    }
+    wscale_group(v, m, t + f);
   }
   double tot;
   if (finish_reduction(s, partial, counter, tot)) apply_op(OP_RNORM, tot, sc, fl);
@@ -196,45 +242,25 @@ __global__ void k_gather_wscale(DevTopo D, const double *xloc, double *out, cons
   if (gidx >= D.nwgrp) return;
   const int f = D.wgrp_first[gidx], m = D.wgrp_size[gidx];
   double g[3] = {0.0, 0.0, 0.0};
-  for (int k = 0; k < m; ++k) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // static indices keep g in registers
     const int r = f + k;
-    g[k] = xloc[D.vec_off[D.lam_sa[r]] + D.lam_da[r]] - xloc[D.vec_off[D.lam_sb[r]] + D.lam_db[r]];
+    if (k < m) g[k] = xloc[D.vec_off[D.lam_sa[r]] + D.lam_da[r]] - xloc[D.vec_off[D.lam_sb[r]] + D.lam_db[r]];
   }
-  constexpr double third = 1.0 / 3.0;
-  if (m == 1) {
-    out[f] = 0.5 * g[0];
-  } else if (m == 2) {
-    out[f] = (2 * g[0] + g[1]) * third;
-    out[f + 1] = (g[0] + 2 * g[1]) * third;
-  } else {
-    out[f] = (3 * g[0] + 2 * g[1] + g[2]) * 0.25;
-    out[f + 1] = (2 * g[0] + 4 * g[1] + 2 * g[2]) * 0.25;
-    out[f + 2] = (g[0] + 2 * g[1] + 3 * g[2]) * 0.25;
-  }
+  wscale_group(g, m, out + f);
 }
 
-// out = W v, W = (B B^T)^{-1}: per node component a chain of m-1 <= 3 rows whose B B^T is
-// tridiag(-1, 2, -1); its inverse in closed form.
+// out = W v (wscale_group per group of W)
 __global__ void k_wscale(DevTopo D, const double *v, double *out, const int *fl) {
   if (fl && fl[FL_DONE]) return;
   const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= D.nwgrp) return;
   const int f = D.wgrp_first[gidx], m = D.wgrp_size[gidx];
-  // multiplications by the constant reciprocals (GB300's FP64 divide is a long instruction
-  // sequence; 1/4 is exact, 1/3 rounds once)
-  constexpr double third = 1.0 / 3.0;
-  if (m == 1) {
-    out[f] = 0.5 * v[f];
-  } else if (m == 2) {
-    const double a = v[f], b = v[f + 1];
-    out[f] = (2 * a + b) * third;
-    out[f + 1] = (a + 2 * b) * third;
-  } else {
-    const double a = v[f], b = v[f + 1], c = v[f + 2];
-    out[f] = (3 * a + 2 * b + c) * 0.25;
-    out[f + 1] = (2 * a + 4 * b + 2 * c) * 0.25;
-    out[f + 2] = (a + 2 * b + 3 * c) * 0.25;
-  }
+  double v3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < m) v3[k] = v[f + k];
+  wscale_group(v3, m, out + f);
 }
 
 // ------------------------------ Dirichlet preconditioner -----------------------------

@@ -144,8 +144,9 @@ def test_graph_kernel_launch_count(F):
     loop body's per round and the inner body's per execution (counted on the device).  With
     pcg_chunk = 1 every inner body is one iteration of Algorithm 1, so two steps that differ in
     iterations but not in restarts differ in launches by a whole number of bodies, and each body
-    holds at least the 15 kernels of one iteration (explicit operators, mixed precision: F 2,
-    projection with its dot product 4, update 1, preconditioner 3, projection 4, p update 1);
+    holds at least the 14 kernels of one iteration (explicit operators, mixed precision: F 2,
+    projection with its dot product 4, update with the preconditioner's W scaling 1,
+    preconditioner 2, projection 4, p update 1);
     without the graph nothing is counted."""
     case = W.small_case(4, 4, 3, k=2, lame_lambda=49.0, tau=1e-3, n_steps=3, tol=1e-10, precision="mixed",
                         source="manufactured_t")
@@ -156,12 +157,12 @@ def test_graph_kernel_launch_count(F):
     sol.factor()
     sts = [sol.step() for _ in range(3)]
     for st in sts:
-        assert st["kernel_launches"] >= 15 * st["iterations"]
+        assert st["kernel_launches"] >= 14 * st["iterations"]
     same = [st for st in sts if st["restarts"] == sts[0]["restarts"]]
     if len(same) >= 2 and same[0]["iterations"] != same[1]["iterations"]:
         diff = same[0]["kernel_launches"] - same[1]["kernel_launches"]
         per_body = diff / (same[0]["iterations"] - same[1]["iterations"])
-        assert per_body == int(per_body) and per_body >= 15
+        assert per_body == int(per_body) and per_body >= 14
     sol.set_option("graph", 0)
     assert sol.step()["kernel_launches"] == -1
     sol.close()
