@@ -78,18 +78,33 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
-// (h, l) += (bh, bl), renormalised
+// (h, l) += (bh, bl), renormalised (by TwoSum: under cancellation of h and bh the collected low
+// parts can exceed the new high part)
 __device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
   float s, e;
   two_sum(h, bh, s, e);
   e += l + bl;
-  h = s + e;
-  l = e - (h - s);
+  two_sum(s, e, h, l);
 }
 // (h, l) = (ah + al) * (xh + xl), dropping al * xl (~2^-48 relative)
 __device__ __forceinline__ void df_mul(float ah, float al, float xh, float xl, float &h, float &l) {
   h = ah * xh;
   l = fmaf(ah, xh, -h) + fmaf(ah, xl, al * xh);
+}
+// (h, l) += (bh, bl) without renormalising: h takes the exact TwoSum, l collects its error and
+// the low parts (long sums; df_norm once before the value is used)
+__device__ __forceinline__ void df_add_lazy(float &h, float &l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  h = s;
+  l += e + bl;
+}
+// TwoSum, not the cheaper fast form: after cancellation in h the low part can be the larger one
+__device__ __forceinline__ void df_norm(float &h, float &l) {
+  float s, e;
+  two_sum(h, l, s, e);
+  h = s;
+  l = e;
 }
 __device__ __forceinline__ void df_split(double v, float &h, float &l) {
   h = (float)v;

@@ -48,7 +48,8 @@ template <typename TO, typename T> __device__ __forceinline__ TO out_of(T v) { r
 template <> __device__ __forceinline__ double out_of<double, dfl>(dfl v) { return to_double(v); }
 // Long sums: a += x * y with the two-float sum left unnormalised (the high part takes the exact
 // TwoSum, the low part collects its error and the product's), so the loop-carried chain is one
-// addition per part; norm() restores h + l with |l| <= ulp(h) / 2 before the value is used.
+// addition per part; norm() restores h + l with |l| <= ulp(h) / 2 before the value is used
+// (TwoSum: after cancellation the low part can be the larger one).
 // float and double: the plain FMA.
 __device__ __forceinline__ void fma_lazy(float &a, float x, float y) { a = fmaf(x, y, a); }
 __device__ __forceinline__ void fma_lazy(double &a, double x, double y) { a = fma(x, y, a); }
@@ -65,11 +66,7 @@ __device__ __forceinline__ void fms_lazy(double &a, double x, double y) { a = fm
 __device__ __forceinline__ void fms_lazy(dfl &a, dfl x, dfl y) { fma_lazy(a, dfl{-x.h, -x.l}, y); }
 __device__ __forceinline__ void norm(float &) {}
 __device__ __forceinline__ void norm(double &) {}
-__device__ __forceinline__ void norm(dfl &a) {
-  const float h = a.h + a.l;
-  a.l = a.l - (h - a.h);
-  a.h = h;
-}
+__device__ __forceinline__ void norm(dfl &a) { df_norm(a.h, a.l); }
 // a -= b
 __device__ __forceinline__ void sub_from(float &a, float b) { a -= b; }
 __device__ __forceinline__ void sub_from(double &a, double b) { a -= b; }
@@ -587,8 +584,9 @@ __global__ void __launch_bounds__(256, 2) k_explicit_apply_sym2f(DevTopo D, cons
       for (int r = 0; r < 32; ++r) {
         float ph, pl;
         df_mul(vh[r], vl[r], xh[32 * I + r], xl[32 * I + r], ph, pl);
-        df_add(sh, sl, ph, pl);
+        df_add_lazy(sh, sl, ph, pl);
       }
+      df_norm(sh, sl);
       cp[tile * 32 + lane] = make_float2(sh, sl);
     }
     const float yh = xh[32 * J + lane], yl = xl[32 * J + lane];
@@ -607,11 +605,12 @@ __global__ void __launch_bounds__(256, 2) k_explicit_apply_sym2f(DevTopo D, cons
         const float sendh = up ? vh[i] : vh[i + k], sendl = up ? vl[i] : vl[i + k];
         float kh = up ? vh[i + k] : vh[i], kl = up ? vl[i + k] : vl[i];
         const float rh = __shfl_xor_sync(FULL, sendh, k), rl = __shfl_xor_sync(FULL, sendl, k);
-        df_add(kh, kl, rh, rl);
+        df_add_lazy(kh, kl, rh, rl);
         vh[i] = kh;
         vl[i] = kl;
       }
     }
+    df_norm(vh[0], vl[0]);
     rp[tile * 32 + lane] = make_float2(vh[0], vl[0]);
   }
   __syncthreads();
@@ -621,11 +620,11 @@ __global__ void __launch_bounds__(256, 2) k_explicit_apply_sym2f(DevTopo D, cons
     float yh = 0.0f, yl = 0.0f;
     for (int J = I; J < nt; ++J) {
       const float2 q = rp[(row0 + J - I) * 32 + r];
-      df_add(yh, yl, q.x, q.y);
+      df_add_lazy(yh, yl, q.x, q.y);
     }
     for (int I2 = 0; I2 < I; ++I2) {
       const float2 q = cp[(I2 * nt - I2 * (I2 - 1) / 2 + I - I2) * 32 + r];
-      df_add(yh, yl, q.x, q.y);
+      df_add_lazy(yh, yl, q.x, q.y);
     }
     x[bnd[i]] = (double)yh + (double)yl;
   }

@@ -508,8 +508,8 @@ __global__ void k_coarse_pack2f(const double *H, int nH, float *tiles) {
 // butterfly over 16 values (offsets 16, 8, 4, 2; lane l ends with row l >> 1 of the half, summed
 // over 16 lanes) and a final exchange with lane l ^ 1.  Transposed product H_IJ^T y_I -> row block
 // J (I < J only) as per-lane sums.  y comes pre-split into two floats (ys: hi at [i], lo at
-// [nH + i]), so the kernel runs no FP64 instruction; partials go to rp[tile] / cp[tile] as
-// two-float pairs.
+// [nH + i]), so the kernel runs no FP64 instruction; sums run unnormalised (df_add_lazy) and are
+// renormalised once; partials go to rp[tile] / cp[tile] as two-float pairs.
 __global__ void __launch_bounds__(256, 4) k_coarse_apply2f(const float *__restrict__ tiles, int nH,
                                                            const float *__restrict__ ys, float2 *rp, float2 *cp,
                                                            const int *fl) {
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(256, 4) k_coarse_apply2f(const float *__restri
         const float xh = row < nH ? __ldg(ys + row) : 0.0f, xl = row < nH ? __ldg(ys + nH + row) : 0.0f;
         float ph, pl;
         df_mul(vh[i], vl[i], xh, xl, ph, pl);
-        df_add(sh, sl, ph, pl);
+        df_add_lazy(sh, sl, ph, pl);
       }
     }
 #pragma unroll
@@ -557,18 +557,22 @@ __global__ void __launch_bounds__(256, 4) k_coarse_apply2f(const float *__restri
         const float sendh = up ? vh[i] : vh[i + cnt], sendl = up ? vl[i] : vl[i + cnt];
         float kh = up ? vh[i + cnt] : vh[i], kl = up ? vl[i + cnt] : vl[i];
         const float rh = __shfl_xor_sync(FULL, sendh, k), rl = __shfl_xor_sync(FULL, sendl, k);
-        df_add(kh, kl, rh, rl);
+        df_add_lazy(kh, kl, rh, rl);
         vh[i] = kh;
         vl[i] = kl;
       }
     }
     {
       const float rh = __shfl_xor_sync(FULL, vh[0], 1), rl = __shfl_xor_sync(FULL, vl[0], 1);
-      df_add(vh[0], vl[0], rh, rl);
+      df_add_lazy(vh[0], vl[0], rh, rl);
+      df_norm(vh[0], vl[0]);
     }
     if ((lane & 1) == 0) rp[(long long)tile * 32 + 16 * half + (lane >> 1)] = make_float2(vh[0], vl[0]);
   }
-  if (I < J) cp[(long long)tile * 32 + lane] = make_float2(sh, sl);
+  if (I < J) {
+    df_norm(sh, sl);
+    cp[(long long)tile * 32 + lane] = make_float2(sh, sl);
+  }
 }
 
 // alpha_i = sum_{J >= I} rp[(I, J)][r] + sum_{J < I} cp[(J, I)][r], i = 32 I + r: one block per
@@ -583,12 +587,13 @@ __global__ void __launch_bounds__(256) k_coarse_sum2f(const float2 *rp, const fl
   float ah = 0.0f, al = 0.0f;
   for (int J = I + w; J < nt; J += 8) {
     const float2 q = rp[(row0 + J - I) * 32 + r];
-    df_add(ah, al, q.x, q.y);
+    df_add_lazy(ah, al, q.x, q.y);
   }
   for (int J = w; J < I; J += 8) {
     const float2 q = cp[((long long)J * nt - (long long)J * (J - 1) / 2 + I - J) * 32 + r];
-    df_add(ah, al, q.x, q.y);
+    df_add_lazy(ah, al, q.x, q.y);
   }
+  df_norm(ah, al);
   part[w][r] = make_float2(ah, al);
   __syncthreads();
   if (w == 0) {
