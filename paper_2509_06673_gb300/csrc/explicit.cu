@@ -330,8 +330,11 @@ __global__ void k_mrhs_symmetrize(DevTopo D, T *out, const long long *out_off, i
 
 // y_b = A_s x_b for every subdomain (A_s = F_s or S_s, dense, row stride mp = m rounded up
 // to 4, pad columns zero), read from and written back to the local vectors at the rows b_s
-// (in place: x_b is staged in shared memory first).  One CTA per subdomain, one warp per
-// row, vectorised row loads; sums in the operator's precision.
+// (in place: x_b is staged in shared memory first).  One CTA per subdomain; a warp takes four
+// rows at a time (vectorised row loads, x read once for the four), accumulates each with plain
+// FMAs and reduces the four lane sums together: two transposing exchanges (offsets 16, 8) leave
+// one row per lane octet, three more steps finish it: 6 additions per lane for four rows
+// instead of 5 per row.  Sums in the operator's precision.
 template <typename T>
 __global__ void __launch_bounds__(256) k_explicit_apply(DevTopo D, const T *ops, const long long *op_off,
                                                         double *xloc, const int *fl) {
@@ -347,23 +350,42 @@ __global__ void __launch_bounds__(256) k_explicit_apply(DevTopo D, const T *ops,
   __syncthreads();
   const T *A = ops + op_off[s];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int a = warp; a < m; a += nw) {
-    const T *row = A + (long long)a * mp;
-    T acc = T(0);
+  for (int a0 = 4 * warp; a0 < m; a0 += 4 * nw) {
+    T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int j = 4 * lane; j < mp; j += 128) {
-      T v[4];
-      if (sizeof(T) == 4) {
-        const float4 f = *reinterpret_cast<const float4 *>(row + j);
-        v[0] = T(f.x); v[1] = T(f.y); v[2] = T(f.z); v[3] = T(f.w);
-      } else {
-        const double2 d0 = *reinterpret_cast<const double2 *>(row + j);
-        const double2 d1 = *reinterpret_cast<const double2 *>(row + j + 2);
-        v[0] = T(d0.x); v[1] = T(d0.y); v[2] = T(d1.x); v[3] = T(d1.y);
+      const T x0 = xs[j], x1 = xs[j + 1], x2 = xs[j + 2], x3 = xs[j + 3];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        if (a0 + rr < m) {
+          const T *row = A + (long long)(a0 + rr) * mp;
+          T v[4];
+          if (sizeof(T) == 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(row + j);
+            v[0] = T(f.x); v[1] = T(f.y); v[2] = T(f.z); v[3] = T(f.w);
+          } else {
+            const double2 d0 = *reinterpret_cast<const double2 *>(row + j);
+            const double2 d1 = *reinterpret_cast<const double2 *>(row + j + 2);
+            v[0] = T(d0.x); v[1] = T(d0.y); v[2] = T(d1.x); v[3] = T(d1.y);
+          }
+          acc[rr] = fma(v[0], x0, acc[rr]);
+          acc[rr] = fma(v[1], x1, acc[rr]);
+          acc[rr] = fma(v[2], x2, acc[rr]);
+          acc[rr] = fma(v[3], x3, acc[rr]);
+        }
       }
-      acc += v[0] * xs[j] + v[1] * xs[j + 1] + v[2] * xs[j + 2] + v[3] * xs[j + 3];
     }
-    acc = warp_sum(acc);
-    if (lane == 0) x[bnd[a]] = double(acc);
+    // lanes with bit 4 set keep rows 2, 3, the others rows 0, 1; then bit 3 picks one of the two
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    T k0 = hi16 ? acc[2] : acc[0], k1 = hi16 ? acc[3] : acc[1];
+    k0 += __shfl_xor_sync(FULL, hi16 ? acc[0] : acc[2], 16);
+    k1 += __shfl_xor_sync(FULL, hi16 ? acc[1] : acc[3], 16);
+    T k = hi8 ? k1 : k0;
+    k += __shfl_xor_sync(FULL, hi8 ? k0 : k1, 8);
+    k += __shfl_xor_sync(FULL, k, 4);
+    k += __shfl_xor_sync(FULL, k, 2);
+    k += __shfl_xor_sync(FULL, k, 1);
+    const int a = a0 + 2 * (hi16 ? 1 : 0) + (hi8 ? 1 : 0);
+    if ((lane & 7) == 0 && a < m) x[bnd[a]] = double(k);
   }
 }
 
