@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_band_factor(const BandTask *tasks, int 
       const int nt = (m + 3) / 4;
       const int npairs = nt * (nt + 1) / 2;
       for (int pidx = threadIdx.x; pidx < npairs; pidx += blockDim.x) {
-        int ti = (int)((sqrt(8.0 * pidx + 1.0) - 1.0) * 0.5);
+        int ti = (int)((sqrtf(8.0f * pidx + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected exactly
         while (ti * (ti + 1) / 2 > pidx) --ti;
         while ((ti + 1) * (ti + 2) / 2 <= pidx) ++ti;
         const int tj = pidx - ti * (ti + 1) / 2;

@@ -475,9 +475,11 @@ cudaError_t launch_gemv(const double *H, const double *y, double *alpha, int nH,
 // tile's partial sums carry ~2^-46 relative error; partials are added in FP64 in a fixed order.
 namespace {
 __device__ __forceinline__ int coarse_tile_row(int tile, int nt) {
-  // largest I with start(I) <= tile
-  const double b = 2.0 * nt + 1.0;
-  int I = (int)floor((b - sqrt(fmax(b * b - 8.0 * tile, 0.0))) * 0.5);
+  // largest I with start(I) <= tile: an FP32 estimate from the quadratic (GB300's FP64 pipe would
+  // make this per-tile index, computed by every lane, the kernel's bottleneck), corrected exactly
+  const long long b = 2LL * nt + 1;
+  const float disc = (float)max(b * b - 8LL * tile, 0LL);
+  int I = (int)(((float)b - sqrtf(disc)) * 0.5f);
   I = max(0, min(I, nt - 1));
   while (I > 0 && I * nt - I * (I - 1) / 2 > tile) --I;
   while (I + 1 < nt && (I + 1) * nt - (I + 1) * I / 2 <= tile) ++I;
