@@ -99,3 +99,20 @@ def test_reference_arm_json_line():
 def test_reference_arm_other_ranks_exit_quietly():
     r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "3"], {"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0 and not r.stdout.strip(), (r.returncode, r.stdout, r.stderr)
+
+
+def test_traffic_record_keyed_on_solve_section(tmp_path, monkeypatch):
+    """The traffic record follows the band solve's source only: an edit above the solve's section
+    of band.cu (the factorisation) keeps it, an edit inside the section drops it."""
+    import bench
+    rec = bench.TRAFFIC_RECORDS[0]
+    src = open(os.path.join(bench.ROOT, "paper_2509_06673_gb300", "csrc", "band.cu"), "rb").read()
+    i = src.find(bench._SOLVE_MARK)
+    assert i > 0
+    fake = tmp_path / "paper_2509_06673_gb300" / "csrc"
+    fake.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (fake / "band.cu").write_bytes(b"// factorisation edited\n" + src[i:])
+    assert bench.traffic_of(rec["workload"], rec["precision"], rec["shape"]) == rec["bytes_per_launch"]
+    (fake / "band.cu").write_bytes(src[i:] + b"// solve edited\n")
+    assert bench.traffic_of(rec["workload"], rec["precision"], rec["shape"]) is None
